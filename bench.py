@@ -1,0 +1,382 @@
+"""Benchmark of the depthwise filtering hot path (forward + both gradients).
+
+Workload (per GPU): 8 x 3 x 4096 x 4096 FP32 images, pixels uniform [0, 1),
+depthwise K x K filters normal(0, 0.1) for K in {3, 7, 15}, clamp border,
+upstream gradient normal(0, 1).  One step = for every K: the forward filter
+and the fused backward pass (input gradient + filter gradient), all through
+the C ABI.  Metric: Gpixel*tap/s = sum_K 3 * N*C*H*W*K^2 / step time.
+
+Prints ONE JSON line.  `--impl reference` times the FP64 CPU oracle (the
+reference arm of this build) on a bounded sample of the same workload.
+Multi-GPU (torchrun): independent replicas, one per GPU, no collective on the
+data path; value = work of all ranks / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N, C, H, W = 8, 3, 4096, 4096
+KS = (3, 7, 15)
+METRIC = "Gpixel*tap/s fwd+bwd (depthwise KxK, K in {3,7,15})"
+UNIT = "Gpixel*tap/s"
+WORKLOAD = "plain_scale: 8x3x4096x4096 fp32, depthwise K in {3,7,15} normal(0,0.1), clamp border, fwd+bwd"
+SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0   # GB300: FP32 FMA units and max clock
+
+
+def peaks():
+    p = {"hbm_gbs": 6800.0, "source": "fallback"}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            m = json.load(f)
+        p = {"hbm_gbs": float(m["hbm_gbs"]), "source": "measured"}
+        mhz = float(m.get("sm_max_mhz", SM_MAX_MHZ))
+    except Exception:
+        mhz = SM_MAX_MHZ
+    # FP32 FMA peak from unit counts and the maximum SM clock (2 flop per FMA)
+    p["fp32_tflops"] = SMS * FP32_LANES * 2 * mhz * 1e6 / 1e12
+    return p
+
+
+def set_images(n: int):
+    global N, WORKLOAD
+    N = n
+    WORKLOAD = WORKLOAD.replace("8x3x4096x4096", f"{n}x3x4096x4096")
+
+
+def taps_per_step():
+    return sum(3 * N * C * H * W * K * K for K in KS)
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        return False
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------- distributed
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def max_over_ranks(value: float, world: int) -> float:
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ------------------------------------------------------------- CPU oracle
+
+def oracle_sample_rate(rows: int = H):
+    """Time the FP64 oracle (fwd + input grad + filter grad for every K) on
+    `rows` x 4096 pixels of one image's 3 channels (default: one whole image
+    of the 8); returns (Gpixel*tap/s, threads, seconds, description)."""
+    import numpy as np
+    import oracle
+    rng = np.random.default_rng(2504)
+    x = rng.random((1, C, rows, W))
+    dy = rng.standard_normal((1, C, rows, W))
+    taps = 0
+    t0 = time.perf_counter()
+    for K in KS:
+        w = rng.normal(0.0, 0.1, (C, K, K))
+        oracle.dw_fwd(x, w, oracle.CLAMP)
+        oracle.dw_bwd_input(dy, w, oracle.CLAMP)
+        oracle.dw_bwd_filter(x, dy, K, oracle.CLAMP)
+        taps += 3 * C * rows * W * K * K
+    dt = time.perf_counter() - t0
+    desc = f"1x{C}x{rows}x{W} band, fwd+bwd_input+bwd_filter for K in {list(KS)}, FP64"
+    return taps / dt / 1e9, oracle.num_threads(), dt, desc
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    rate_rows = 256
+    times = []
+    for step in range(args.warmup + args.steps):
+        v, cores, dt, desc = oracle_sample_rate(rate_rows)
+        if step >= args.warmup:
+            times.append((v, dt))
+    value = statistics.median(v for v, _ in times)
+    ms = statistics.median(dt for _, dt in times) * 1e3
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": desc, "l2": "n/a (host)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------------- GPU
+
+def run_giga(args):
+    import torch
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+
+    from paper_2504_01266_gb300 import _lib, build
+    build.build()
+    L = _lib
+    L.load()
+
+    g = torch.Generator(device=dev)
+    g.manual_seed(2504 + 1)
+    x = torch.rand((N, C, H, W), generator=g, device=dev)
+    dy = torch.randn((N, C, H, W), generator=g, device=dev)
+    ws_cpu = torch.Generator().manual_seed(2505)
+    filt = {K: (torch.randn((C, K, K), generator=ws_cpu) * 0.1).to(dev) for K in KS}
+    y = torch.empty_like(x)
+    dx = torch.empty_like(x)
+    dws = {K: torch.empty((C, K, K), device=dev) for K in KS}
+    descs = {K: L.desc(N, C, C, H, W, K, C, L.GIGA_BORDER_CLAMP, L.GIGA_F32,
+                       L.GIGA_LAYOUT_NCHW) for K in KS}
+    ws_bytes = max(L.giga_conv2d_workspace_size(descs[K], L.GIGA_OP_BWD_INPUT |
+                                                L.GIGA_OP_BWD_FILTER) for K in KS)
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    sp = stream.cuda_stream
+
+    # per-op events on the launching stream: (K, op) -> list of ms
+    op_ms = {(K, op): [] for K in KS for op in ("fwd", "bwd")}
+
+    def step(record=False):
+        for K in KS:
+            d = descs[K]
+            if record:
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e2 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+            L.check(L.giga_conv2d_fwd(d, x.data_ptr(), filt[K].data_ptr(), y.data_ptr(),
+                                      None, 0, sp), "fwd")
+            if record:
+                e1.record(stream)
+            L.check(L.giga_conv2d_bwd(d, x.data_ptr(), dy.data_ptr(), filt[K].data_ptr(),
+                                      dx.data_ptr(), dws[K].data_ptr(), ws.data_ptr(),
+                                      ws_bytes, sp), "bwd")
+            if record:
+                e2.record(stream)
+                op_ms[(K, "fwd")].append((e0, e1))
+                op_ms[(K, "bwd")].append((e1, e2))
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize(dev)
+
+    L.giga_launch_count_reset()
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(dev.index if dev.index is not None else 0) as clocks:
+        start.record(stream)
+        for _ in range(args.steps):
+            step(record=True)
+        end.record(stream)
+        torch.cuda.synchronize(dev)
+    launches = L.giga_launch_count()
+    barrier(world)
+    ms_local = start.elapsed_time(end) / args.steps
+    ms = max_over_ranks(ms_local, world)
+    value = world * taps_per_step() / (ms * 1e-3) / 1e9
+
+    # per-op roofline from the events recorded inside the timed region
+    pk = peaks()
+    px = N * C * H * W
+    ops = []
+    for (K, op), evs in op_ms.items():
+        t = statistics.mean(a.elapsed_time(b) for a, b in evs) * 1e-3
+        bytes_ = px * (8 if op == "fwd" else 12)
+        fma = px * K * K * (1 if op == "fwd" else 2)
+        t_hbm = bytes_ / (pk["hbm_gbs"] * 1e9)
+        t_alu = 2 * fma / (pk["fp32_tflops"] * 1e12)
+        if t_hbm >= t_alu:
+            ach, peak, unit, bound, traffic = bytes_ / t / 1e9, pk["hbm_gbs"], "GB/s", "hbm", bytes_
+        else:
+            ach, peak, unit, bound, traffic = 2 * fma / t / 1e12, pk["fp32_tflops"], "TFLOP/s", "alu", None
+        ops.append({"K": K, "op": op, "ms": t * 1e3, "bound": bound, "achieved": ach,
+                    "peak": peak, "unit": unit, "frac": ach / peak,
+                    "gbs": bytes_ / t / 1e9, "tflops": 2 * fma / t / 1e12})
+    dom = max(ops, key=lambda o: o["ms"])
+    roofline = {"bound": dom["bound"], "achieved": dom["achieved"], "peak": dom["peak"],
+                "unit": dom["unit"], "frac": dom["frac"], "traffic": None,
+                "kernel": f"{dom['op']} K={dom['K']}",
+                "peak_source": (f"{pk['source']} HBM copy" if dom["bound"] == "hbm" else
+                                "FP32 FMA: 152 SMs x 128 lanes x 2 x max SM clock")}
+
+    # end to end through the C ABI with host buffers (pinned), copies timed
+    e2e = None
+    if not args.no_e2e:
+        hx = torch.empty((N, C, H, W), pin_memory=True)
+        hdy = torch.empty((N, C, H, W), pin_memory=True)
+        hx.copy_(x.cpu())
+        hdy.copy_(dy.cpu())
+        hy = torch.empty((N, C, H, W), pin_memory=True)
+        hdx = torch.empty((N, C, H, W), pin_memory=True)
+        hdw = {K: torch.empty((C, K, K), pin_memory=True) for K in KS}
+        torch.cuda.synchronize(dev)
+        e_steps = max(1, min(args.steps, 3))
+        barrier(world)
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        for _ in range(e_steps):
+            x.copy_(hx, non_blocking=True)
+            dy.copy_(hdy, non_blocking=True)
+            for K in KS:
+                d = descs[K]
+                L.check(L.giga_conv2d_fwd(d, x.data_ptr(), filt[K].data_ptr(), y.data_ptr(),
+                                          None, 0, sp), "fwd")
+                L.check(L.giga_conv2d_bwd(d, x.data_ptr(), dy.data_ptr(), filt[K].data_ptr(),
+                                          dx.data_ptr(), dws[K].data_ptr(), ws.data_ptr(),
+                                          ws_bytes, sp), "bwd")
+                hy.copy_(y, non_blocking=True)
+                hdx.copy_(dx, non_blocking=True)
+                hdw[K].copy_(dws[K], non_blocking=True)
+        s1.record(stream)
+        torch.cuda.synchronize(dev)
+        e_ms = max_over_ranks(s0.elapsed_time(s1) / e_steps, world)
+        elem = 4
+        e2e = {"value": world * taps_per_step() / (e_ms * 1e-3) / 1e9, "unit": UNIT,
+               "ms_per_step": e_ms,
+               "h2d_bytes_per_step": 2 * px * elem,
+               "d2h_bytes_per_step": len(KS) * (2 * px * elem) + sum(C * K * K * 4 for K in KS)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        v, cores, dt, desc = oracle_sample_rate()
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{desc}; {dt:.1f} s"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "N": N, "C": C, "H": H, "W": W, "K": list(KS),
+                       "border": "clamp", "parallelism": f"replicas{world}",
+                       "l2": "inputs larger than L2 (1.6 GB per tensor), no flush"},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clocks.summary(),
+            "ops": ops,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="giga", choices=["giga", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--images", type=int, default=N,
+                    help="images per GPU (profiling runs use 1: 201 MB per tensor, above L2)")
+    args = ap.parse_args()
+    if args.images != N:
+        set_images(args.images)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_giga(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,191 @@
+/*
+ * giga.h -- C ABI of libgiga: dense 2D image filtering on one GB300 (sm_103a).
+ *
+ * The operation is the neighbourhood sum of the GigaAPI paper (Section 4.2.4,
+ * "Sharpening"): every output pixel of every channel is the weighted sum of the
+ * K x K neighbourhood centred on it, each neighbour multiplied by the filter
+ * entry at the same offset from the filter centre (a cross-correlation; the
+ * filter is not flipped).  Neighbours outside the image read zero (the paper
+ * skips them: GIGA_BORDER_ZERO) or the nearest edge pixel, clamped per axis
+ * (GIGA_BORDER_CLAMP).  With r = (K - 1) / 2 and the border rule applied to x:
+ *
+ *   depthwise (NCHW, w[C][K][K]):
+ *     y[n][c][i][j] = sum_{a,b < K} w[c][a][b] * x[n][c][i + a - r][j + b - r]
+ *   dense (NHWC, w[Co][K][K][Ci]):
+ *     y[n][i][j][o] = sum_{a,b,c} w[o][a][b][c] * x[n][i + a - r][j + b - r][c]
+ *
+ * The gradients are the exact adjoints: dx = K^T dy (for the clamp border the
+ * contributions that were read from clamped positions return to the edge pixel
+ * they were read from) and dw[c][a][b] = sum_{n,i,j} dy[n][c][i][j] *
+ * x[n][c][i + a - r][j + b - r] (the filter is shared by the batch, so the sum
+ * runs over n).  The filter gradient is reduced in FP64 in a fixed order, so
+ * repeated calls on the same device give bit-identical results.
+ *
+ * Conventions for every entry point:
+ *   - Every pointer argument named x, y, dx, dy, w, dw, ws is a DEVICE pointer
+ *     owned by the caller; the library never allocates device memory and never
+ *     keeps a pointer after the call returns (batched plans keep host copies of
+ *     their descriptors, see below).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Every launch is asynchronous on that stream; nothing synchronises the
+ *     host unless stated.  The calls are safe to capture into a CUDA graph
+ *     (the autotuner never benchmarks while the stream is capturing).
+ *   - Argument errors are detected before any launch and return a status
+ *     without touching memory; `giga_last_error_detail()` then describes the
+ *     problem (thread-local).  A failed launch returns GIGA_ERR_CUDA.  No C++
+ *     exception crosses this boundary.
+ *   - Supported: odd K in [1, 31] (the filter gradient and the batched path:
+ *     K <= 15); FP32 or BF16 storage for depthwise (weights, accumulation and
+ *     dw always FP32); BF16 storage for dense (3 x 3, C_in = C_out = 64,
+ *     zero border; dw FP32).  Tensors are dense and contiguous.
+ *   - Inputs and outputs must not alias (y != x, dx != dy).
+ */
+#ifndef GIGA_H
+#define GIGA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t giga_status_t;
+enum {
+    GIGA_OK = 0,
+    GIGA_ERR_INVALID_ARG = 1, /* bad shape, K, enum, NULL pointer or aliasing */
+    GIGA_ERR_UNSUPPORTED = 2, /* valid but not implemented (e.g. dense FP32)   */
+    GIGA_ERR_MISALIGNED = 3,  /* pointer not aligned to its element size       */
+    GIGA_ERR_WORKSPACE = 4,   /* workspace NULL, too small or not 256-B aligned */
+    GIGA_ERR_CUDA = 5,        /* a CUDA call or launch failed                   */
+    GIGA_ERR_TIMEOUT = 6      /* reserved: a bounded device wait gave up        */
+};
+
+enum { GIGA_BORDER_ZERO = 0, GIGA_BORDER_CLAMP = 1 };
+enum { GIGA_F32 = 0, GIGA_BF16 = 1 };
+enum { GIGA_LAYOUT_NCHW = 0, GIGA_LAYOUT_NHWC = 1 };
+enum { GIGA_OP_FWD = 1, GIGA_OP_BWD_INPUT = 2, GIGA_OP_BWD_FILTER = 4 };
+
+/* Problem descriptor (host memory, read during the call only).
+ *   groups == C_in == C_out  -> depthwise, layout NCHW, dtype F32 or BF16
+ *   groups == 1              -> dense, layout NHWC, dtype BF16
+ * N, C, H, W may be 0 (nothing is launched; dw is zeroed). */
+typedef struct {
+    int64_t N, C_in, C_out, H, W;
+    int32_t K;
+    int32_t groups;
+    int32_t border; /* GIGA_BORDER_* */
+    int32_t dtype;  /* GIGA_F32 / GIGA_BF16: storage of x, y, dx, dy */
+    int32_t layout; /* GIGA_LAYOUT_* */
+    int32_t reserved; /* must be 0 */
+} giga_conv2d_desc_t;
+
+/* Bytes of device workspace the ops in `ops` (GIGA_OP_* bitmask) need for
+ * this descriptor.  0 means no workspace.  Workspaces must be 256-B aligned. */
+giga_status_t giga_conv2d_workspace_size(const giga_conv2d_desc_t* desc, int32_t ops,
+                                         size_t* bytes);
+
+/* Forward filter (Section 4.2.4): y = K_w x.  Depthwise: x, y [N][C][H][W]
+ * (dtype), w [C][K][K] FP32.  Dense: x [N][H][W][Ci], y [N][H][W][Co] BF16,
+ * w [Co][K][K][Ci] BF16.  ws may be NULL when the size query returned 0. */
+giga_status_t giga_conv2d_fwd(const giga_conv2d_desc_t* desc, const void* x, const void* w,
+                              void* y, void* ws, size_t ws_bytes, void* stream);
+
+/* Input gradient dx = K_w^T dy (same layouts as x / y). */
+giga_status_t giga_conv2d_bwd_input(const giga_conv2d_desc_t* desc, const void* dy,
+                                    const void* w, void* dx, void* ws, size_t ws_bytes,
+                                    void* stream);
+
+/* Filter gradient dw = d<K_w x, dy>/dw, FP32, same layout as w.  Per-CTA FP32
+ * partial sums go to the workspace and are summed in FP64 in a fixed order. */
+giga_status_t giga_conv2d_bwd_filter(const giga_conv2d_desc_t* desc, const void* x,
+                                     const void* dy, float* dw, void* ws, size_t ws_bytes,
+                                     void* stream);
+
+/* Both gradients in one fused pass that reads x and dy once (depthwise only;
+ * needs the workspace of GIGA_OP_BWD_INPUT | GIGA_OP_BWD_FILTER). */
+giga_status_t giga_conv2d_bwd(const giga_conv2d_desc_t* desc, const void* x, const void* dy,
+                              const float* w, void* dx, float* dw, void* ws, size_t ws_bytes,
+                              void* stream);
+
+/* ------------------------------------------------------------------------
+ * Ragged batches (the paper's unfinished "database of images", Section 5):
+ * images of different sizes, each with its own depthwise filters, processed
+ * by ONE persistent launch that pulls work from a tile table.
+ *
+ * One entry per image; all pointers are device pointers, NCHW with N = 1:
+ *   x, y, dy, dx: [C][H][W] in the batch dtype; w, dw: [C][K][K] FP32.
+ * Pointers of ops that are not requested may be NULL. */
+typedef struct {
+    const void* x;
+    void* y;
+    const void* dy;
+    void* dx;
+    const float* w;
+    float* dw;
+    int32_t H, W, C, K;
+} giga_image_t;
+
+typedef struct giga_batched_plan_s* giga_batched_plan_t;
+
+/* Build the tile table on the host (sorted by cost, longest first).  `ops` is
+ * a GIGA_OP_* bitmask; border and dtype apply to every image.  The plan copies
+ * the descriptors; it owns host memory only. */
+giga_status_t giga_batched_plan_create(const giga_image_t* images, int32_t n, int32_t ops,
+                                       int32_t border, int32_t dtype,
+                                       giga_batched_plan_t* plan);
+giga_status_t giga_batched_plan_workspace_size(giga_batched_plan_t plan, size_t* bytes);
+/* Copy the tile table into the workspace (asynchronous on `stream`; the plan
+ * must outlive the copy -- giga_batched_plan_destroy waits for it). */
+giga_status_t giga_batched_plan_upload(giga_batched_plan_t plan, void* ws, size_t ws_bytes,
+                                       void* stream);
+/* One persistent launch for all images (plus a memset of its counters).
+ * Capturable into a CUDA graph once the table has been uploaded. */
+giga_status_t giga_batched_plan_run(giga_batched_plan_t plan, void* ws, size_t ws_bytes,
+                                    void* stream);
+void giga_batched_plan_destroy(giga_batched_plan_t plan);
+
+/* Convenience: create + upload + run + destroy (blocks until the table copy
+ * has left host memory; not capturable). */
+giga_status_t giga_conv2d_batched(const giga_image_t* images, int32_t n, int32_t ops,
+                                  int32_t border, int32_t dtype, void* ws, size_t ws_bytes,
+                                  void* stream);
+giga_status_t giga_conv2d_batched_workspace_size(const giga_image_t* images, int32_t n,
+                                                 int32_t ops, size_t* bytes);
+
+/* ------------------------------------------------------------------------
+ * Autotuner.  Candidates: tile height / rows per thread / tiles per CTA.
+ * Modes (also from the environment variable GIGA_AUTOTUNE=off|cached|full):
+ *   0 off:    always the built-in default configuration;
+ *   1 cached: use a cached choice when one exists (default);
+ *   2 full:   like cached, and the entry points benchmark the candidates the
+ *             first time they meet an uncached problem class (not while the
+ *             stream is capturing).
+ * The cache is kept in memory and, if GIGA_AUTOTUNE_CACHE names a file,
+ * loaded from / saved to it as JSON.  A corrupt cache file is ignored. */
+giga_status_t giga_autotune_set_mode(int32_t mode);
+int32_t giga_autotune_get_mode(void);
+/* Benchmark every candidate for this problem on the given buffers (outputs
+ * are overwritten; synchronises `stream`) and record the fastest. */
+giga_status_t giga_autotune_conv2d(const giga_conv2d_desc_t* desc, int32_t ops, const void* x,
+                                   const void* w, void* y, const void* dy, void* dx, float* dw,
+                                   void* ws, size_t ws_bytes, void* stream);
+/* The configuration id the entry points will use for (desc, op); -1 on error. */
+int32_t giga_autotune_choice(const giga_conv2d_desc_t* desc, int32_t op);
+giga_status_t giga_autotune_save(const char* path);
+giga_status_t giga_autotune_load(const char* path);
+void giga_autotune_clear(void);
+
+/* ------------------------------------------------------------------------ */
+const char* giga_status_string(giga_status_t status);
+/* Description of the last error on the calling thread ("" if none). */
+const char* giga_last_error_detail(void);
+/* Kernel launches issued by this library on the calling thread since the last
+ * reset (for launch accounting in benchmarks). */
+uint64_t giga_launch_count(void);
+void giga_launch_count_reset(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GIGA_H */

@@ -1,0 +1,154 @@
+"""GB300-native dense 2D image filtering (the sharpening filter of the GigaAPI
+paper, Section 4.2.4, widened to K x K depthwise/dense filters, zero/clamp
+borders, both gradients, ragged batches and BF16 storage).
+
+PyTorch supplies device memory and streams; every step of the filtering path
+runs in libgiga's CUDA kernels behind the C ABI of include/giga.h.  The
+helpers below allocate outputs and workspaces with torch and marshal pointers
+through ``_lib``.  There is no CPU fallback: calling them without the built
+library or without a CUDA tensor raises.
+
+Conventions: depthwise tensors NCHW (FP32 or BF16) with FP32 filters
+``w[C][K][K]`` (cross-correlation, tap (a, b) reads pixel (i + a - r, j + b - r));
+border "zero" or "clamp".
+"""
+from __future__ import annotations
+
+import torch
+
+from . import _lib
+
+BORDERS = {"zero": _lib.GIGA_BORDER_ZERO, "clamp": _lib.GIGA_BORDER_CLAMP}
+DTYPES = {torch.float32: _lib.GIGA_F32, torch.bfloat16: _lib.GIGA_BF16}
+
+__all__ = ["conv2d", "conv2d_fwd", "conv2d_bwd", "conv2d_bwd_input", "conv2d_bwd_filter",
+           "DepthwiseConv2d", "workspace", "BORDERS"]
+
+
+def _border(border) -> int:
+    if isinstance(border, str):
+        if border not in BORDERS:
+            raise ValueError(f"border must be one of {list(BORDERS)}")
+        return BORDERS[border]
+    return int(border)
+
+
+def _dtype(t: torch.Tensor) -> int:
+    if t.dtype not in DTYPES:
+        raise TypeError(f"unsupported dtype {t.dtype}: use float32 or bfloat16")
+    return DTYPES[t.dtype]
+
+
+def _require_cuda(*ts):
+    for t in ts:
+        if t is not None and not t.is_cuda:
+            raise RuntimeError("libgiga runs on CUDA tensors only (no CPU fallback)")
+        if t is not None and not t.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+
+
+def _stream(device) -> int:
+    return torch.cuda.current_stream(device).cuda_stream
+
+
+def dw_desc(x: torch.Tensor, K: int, border) -> _lib.giga_conv2d_desc_t:
+    N, C, H, W = x.shape
+    return _lib.desc(N, C, C, H, W, K, C, _border(border), _dtype(x), _lib.GIGA_LAYOUT_NCHW)
+
+
+def workspace(d: _lib.giga_conv2d_desc_t, ops: int, device) -> torch.Tensor | None:
+    n = _lib.giga_conv2d_workspace_size(d, ops)
+    if n == 0:
+        return None
+    return torch.empty(n, dtype=torch.uint8, device=device)
+
+
+def _ptr(t):
+    return None if t is None else t.data_ptr()
+
+
+def _nbytes(t):
+    return 0 if t is None else t.numel()
+
+
+def conv2d_fwd(x: torch.Tensor, w: torch.Tensor, border="zero", out=None) -> torch.Tensor:
+    """y = K_w x (depthwise, NCHW)."""
+    _require_cuda(x, w)
+    d = dw_desc(x, w.shape[-1], border)
+    y = torch.empty_like(x) if out is None else out
+    ws = workspace(d, _lib.GIGA_OP_FWD, x.device)
+    _lib.check(_lib.giga_conv2d_fwd(d, _ptr(x), _ptr(w), _ptr(y), _ptr(ws), _nbytes(ws),
+                                    _stream(x.device)), "giga_conv2d_fwd")
+    return y
+
+
+def conv2d_bwd_input(dy: torch.Tensor, w: torch.Tensor, border="zero", out=None):
+    """dx = K_w^T dy."""
+    _require_cuda(dy, w)
+    d = dw_desc(dy, w.shape[-1], border)
+    dx = torch.empty_like(dy) if out is None else out
+    ws = workspace(d, _lib.GIGA_OP_BWD_INPUT, dy.device)
+    _lib.check(_lib.giga_conv2d_bwd_input(d, _ptr(dy), _ptr(w), _ptr(dx), _ptr(ws),
+                                          _nbytes(ws), _stream(dy.device)),
+               "giga_conv2d_bwd_input")
+    return dx
+
+
+def conv2d_bwd_filter(x: torch.Tensor, dy: torch.Tensor, K: int, border="zero", out=None):
+    """dw[c][a][b] = sum_{n,i,j} dy * x~ (FP32, shape (C, K, K))."""
+    _require_cuda(x, dy)
+    d = dw_desc(x, K, border)
+    dw = torch.empty((x.shape[1], K, K), dtype=torch.float32, device=x.device) \
+        if out is None else out
+    ws = workspace(d, _lib.GIGA_OP_BWD_FILTER, x.device)
+    _lib.check(_lib.giga_conv2d_bwd_filter(d, _ptr(x), _ptr(dy), _ptr(dw), _ptr(ws),
+                                           _nbytes(ws), _stream(x.device)),
+               "giga_conv2d_bwd_filter")
+    return dw
+
+
+def conv2d_bwd(x: torch.Tensor, dy: torch.Tensor, w: torch.Tensor, border="zero",
+               dx=None, dw=None, ws=None):
+    """Fused (dx, dw) in one pass over x and dy."""
+    _require_cuda(x, dy, w)
+    K = w.shape[-1]
+    d = dw_desc(x, K, border)
+    dx = torch.empty_like(dy) if dx is None else dx
+    dw = torch.empty((x.shape[1], K, K), dtype=torch.float32, device=x.device) \
+        if dw is None else dw
+    if ws is None:
+        ws = workspace(d, _lib.GIGA_OP_BWD_INPUT | _lib.GIGA_OP_BWD_FILTER, x.device)
+    _lib.check(_lib.giga_conv2d_bwd(d, _ptr(x), _ptr(dy), _ptr(w), _ptr(dx), _ptr(dw),
+                                    _ptr(ws), _nbytes(ws), _stream(x.device)),
+               "giga_conv2d_bwd")
+    return dx, dw
+
+
+class DepthwiseConv2d(torch.autograd.Function):
+    """Autograd wrapper: forward = giga_conv2d_fwd, backward = the fused
+    giga_conv2d_bwd (or one of the two gradients when only one is needed)."""
+
+    @staticmethod
+    def forward(ctx, x, w, border="zero"):
+        ctx.border = border
+        ctx.save_for_backward(x, w)
+        return conv2d_fwd(x.contiguous(), w.contiguous(), border)
+
+    @staticmethod
+    def backward(ctx, dy):
+        x, w = ctx.saved_tensors
+        dy = dy.contiguous().to(x.dtype)
+        need_x, need_w = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
+        dx = dw = None
+        if need_x and need_w:
+            dx, dw = conv2d_bwd(x, dy, w, ctx.border)
+        elif need_x:
+            dx = conv2d_bwd_input(dy, w, ctx.border)
+        elif need_w:
+            dw = conv2d_bwd_filter(x, dy, w.shape[-1], ctx.border)
+        return dx, dw, None
+
+
+def conv2d(x: torch.Tensor, w: torch.Tensor, border="zero") -> torch.Tensor:
+    """Depthwise K x K filtering with autograd support."""
+    return DepthwiseConv2d.apply(x, w, border)

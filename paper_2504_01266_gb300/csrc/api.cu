@@ -1,0 +1,403 @@
+// api.cu -- the C ABI of libgiga (include/giga.h): argument validation,
+// workspace sizing, dispatch to the depthwise kernels, status reporting.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdint>
+#include <cstring>
+#include <string>
+
+#include "dw_launch.h"
+#include "internal.h"
+
+namespace giga {
+
+static thread_local std::string t_error;
+static thread_local uint64_t t_launches = 0;
+
+void note_launch(int n) { t_launches += (uint64_t)n; }
+
+giga_status_t fail(giga_status_t status, const std::string& detail) {
+  t_error = detail;
+  return status;
+}
+
+giga_status_t cuda_fail(cudaError_t e, const char* where) {
+  return fail(GIGA_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+void clear_error() { t_error.clear(); }
+
+int sm_count() {
+  static std::atomic<int> cached[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 148;
+  int v = cached[dev].load();
+  if (v == 0) {
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0)
+      v = 148;
+    cached[dev].store(v);
+  }
+  return v;
+}
+
+// ------------------------------------------------------------ validation
+
+static bool is_depthwise(const giga_conv2d_desc_t* d) {
+  return d->groups == d->C_in && d->C_out == d->C_in;
+}
+
+static giga_status_t check_desc(const giga_conv2d_desc_t* d) {
+  if (!d) return fail(GIGA_ERR_INVALID_ARG, "desc is NULL");
+  if (d->reserved != 0) return fail(GIGA_ERR_INVALID_ARG, "desc.reserved must be 0");
+  if (d->N < 0 || d->C_in < 0 || d->C_out < 0 || d->H < 0 || d->W < 0)
+    return fail(GIGA_ERR_INVALID_ARG, "negative dimension");
+  if (d->K < 1 || d->K > 31 || (d->K % 2) == 0)
+    return fail(GIGA_ERR_INVALID_ARG, "K must be odd and in [1, 31], got " + std::to_string(d->K));
+  if (d->border != GIGA_BORDER_ZERO && d->border != GIGA_BORDER_CLAMP)
+    return fail(GIGA_ERR_INVALID_ARG, "unknown border " + std::to_string(d->border));
+  if (d->dtype != GIGA_F32 && d->dtype != GIGA_BF16)
+    return fail(GIGA_ERR_INVALID_ARG, "unknown dtype " + std::to_string(d->dtype));
+  if (d->layout != GIGA_LAYOUT_NCHW && d->layout != GIGA_LAYOUT_NHWC)
+    return fail(GIGA_ERR_INVALID_ARG, "unknown layout " + std::to_string(d->layout));
+  if (d->H >= (1LL << 31) || d->W >= (1LL << 31) || d->H * d->W >= (1LL << 40))
+    return fail(GIGA_ERR_INVALID_ARG, "image too large");
+  if (is_depthwise(d)) {
+    if (d->layout != GIGA_LAYOUT_NCHW)
+      return fail(GIGA_ERR_UNSUPPORTED, "depthwise filtering takes NCHW tensors");
+    return GIGA_OK;
+  }
+  if (d->groups != 1)
+    return fail(GIGA_ERR_INVALID_ARG, "groups must be C_in (depthwise, C_out == C_in) or 1 (dense)");
+  return GIGA_OK;
+}
+
+static size_t elem_size(int dtype) { return dtype == GIGA_BF16 ? 2 : 4; }
+
+static giga_status_t check_ptr(const void* p, size_t numel, size_t align, const char* name) {
+  if (numel == 0) return GIGA_OK;
+  if (!p) return fail(GIGA_ERR_INVALID_ARG, std::string(name) + " is NULL");
+  if (reinterpret_cast<uintptr_t>(p) % align)
+    return fail(GIGA_ERR_MISALIGNED, std::string(name) + " is not aligned to its element size");
+  return GIGA_OK;
+}
+
+static bool overlap(const void* a, const void* b, size_t bytes) {
+  if (!a || !b || bytes == 0) return false;
+  auto x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+  return x < y + bytes && y < x + bytes;
+}
+
+static int64_t dw_planes(const giga_conv2d_desc_t* d) { return d->N * d->C_in; }
+static int64_t dw_numel(const giga_conv2d_desc_t* d) { return dw_planes(d) * d->H * d->W; }
+
+static DwArgs make_args(const giga_conv2d_desc_t* d) {
+  DwArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.N = d->N;
+  a.C = d->C_in;
+  a.H = d->H;
+  a.W = d->W;
+  a.K = d->K;
+  a.border = d->border;
+  a.dtype = d->dtype;
+  return a;
+}
+
+// 128-bit (f32) / 64-bit (bf16) row accesses need aligned bases and W % 4 == 0.
+static int vec_ok(const DwArgs& a, const void* p0, const void* p1, const void* p2) {
+  const uintptr_t align = a.dtype == GIGA_F32 ? 16 : 8;
+  if (a.W % 4) return 0;
+  for (const void* p : {p0, p1, p2})
+    if (p && reinterpret_cast<uintptr_t>(p) % align) return 0;
+  return 1;
+}
+
+// Filter-gradient workspace: per-CTA partials at the smallest tiles-per-CTA
+// any configuration uses (1), so every autotuner choice fits.
+static size_t dw_filter_ws(const giga_conv2d_desc_t* d) {
+  const int64_t chunks = dw_bwd_chunks_per_plane(d->H, d->W, 1);
+  size_t bytes = (size_t)dw_planes(d) * (size_t)chunks * (size_t)(d->K * d->K) * sizeof(float);
+  return (bytes + 255) / 256 * 256;
+}
+
+static giga_status_t check_ws(void* ws, size_t ws_bytes, size_t need) {
+  if (need == 0) return GIGA_OK;
+  if (!ws) return fail(GIGA_ERR_WORKSPACE, "workspace is NULL, need " + std::to_string(need));
+  if (ws_bytes < need)
+    return fail(GIGA_ERR_WORKSPACE, "workspace of " + std::to_string(ws_bytes) +
+                                        " bytes is too small, need " + std::to_string(need));
+  if (reinterpret_cast<uintptr_t>(ws) % 256)
+    return fail(GIGA_ERR_WORKSPACE, "workspace must be 256-byte aligned");
+  return GIGA_OK;
+}
+
+// --------------------------------------------------------------- dispatch
+
+template <typename F>
+static cudaError_t dispatch_k(int K, F&& f) {
+  switch (K) {
+#define GIGA_CASE(k) \
+  case k:            \
+    return f(std::integral_constant<int, k>{});
+    GIGA_CASE(1) GIGA_CASE(3) GIGA_CASE(5) GIGA_CASE(7) GIGA_CASE(9) GIGA_CASE(11)
+    GIGA_CASE(13) GIGA_CASE(15) GIGA_CASE(17) GIGA_CASE(19) GIGA_CASE(21) GIGA_CASE(23)
+    GIGA_CASE(25) GIGA_CASE(27) GIGA_CASE(29) GIGA_CASE(31)
+#undef GIGA_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+template <typename F>
+static cudaError_t dispatch_k_filter(int K, F&& f) {
+  switch (K) {
+#define GIGA_CASE(k) \
+  case k:            \
+    return f(std::integral_constant<int, k>{});
+    GIGA_CASE(1) GIGA_CASE(3) GIGA_CASE(5) GIGA_CASE(7) GIGA_CASE(9) GIGA_CASE(11)
+    GIGA_CASE(13) GIGA_CASE(15)
+#undef GIGA_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+giga_status_t run_dw_op(int op, const DwArgs& a, const DwConfig& cfg, cudaStream_t st) {
+  cudaError_t e = cudaSuccess;
+  switch (op) {
+    case TUNE_FWD:
+      e = dispatch_k(a.K, [&](auto k) { return dw_fwd_launch<decltype(k)::value>(a, cfg, false, st); });
+      if (e != cudaSuccess) return cuda_fail(e, "forward launch");
+      return GIGA_OK;
+    case TUNE_BWD_INPUT:
+      e = dispatch_k(a.K, [&](auto k) { return dw_fwd_launch<decltype(k)::value>(a, cfg, true, st); });
+      if (e == cudaSuccess) e = dw_fixup_launch(a, st);
+      if (e != cudaSuccess) return cuda_fail(e, "input-gradient launch");
+      return GIGA_OK;
+    case TUNE_BWD_FILTER:
+    case TUNE_BWD_FUSED: {
+      const int mode = op == TUNE_BWD_FUSED ? 0 : 1;
+      e = dispatch_k_filter(a.K, [&](auto k) { return dw_bwd_launch<decltype(k)::value>(a, cfg, mode, st); });
+      if (e == cudaSuccess && mode == 0) e = dw_fixup_launch(a, st);
+      if (e == cudaSuccess)
+        e = dw_finalize_launch(a, dw_bwd_chunks_per_plane(a.H, a.W, cfg.tiles_per_cta), st);
+      if (e != cudaSuccess) return cuda_fail(e, "backward launch");
+      return GIGA_OK;
+    }
+  }
+  return fail(GIGA_ERR_INVALID_ARG, "unknown op");
+}
+
+static bool stream_capturing(cudaStream_t st) {
+  cudaStreamCaptureStatus s = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &s) != cudaSuccess) return true;
+  return s != cudaStreamCaptureStatusNone;
+}
+
+static giga_status_t run_tuned(int op, const DwArgs& a, cudaStream_t st) {
+  int id = tune_mode() == 0 ? 0 : tune_lookup(op, a);
+  if (id < 0 && tune_mode() == 2 && !stream_capturing(st)) {
+    giga_status_t s = tune_dw_op(op, a, st);
+    if (s != GIGA_OK) return s;
+    id = tune_lookup(op, a);
+  }
+  if (id < 0) id = 0;
+  return run_dw_op(op, a, tune_config(op, id, a), st);
+}
+
+}  // namespace giga
+
+using namespace giga;
+
+// ------------------------------------------------------------------ C ABI
+
+extern "C" {
+
+giga_status_t giga_conv2d_workspace_size(const giga_conv2d_desc_t* desc, int32_t ops,
+                                         size_t* bytes) {
+  clear_error();
+  if (!bytes) return fail(GIGA_ERR_INVALID_ARG, "bytes is NULL");
+  *bytes = 0;
+  giga_status_t s = check_desc(desc);
+  if (s != GIGA_OK) return s;
+  if (ops & ~(GIGA_OP_FWD | GIGA_OP_BWD_INPUT | GIGA_OP_BWD_FILTER))
+    return fail(GIGA_ERR_INVALID_ARG, "unknown op bits");
+  if (!is_depthwise(desc)) return GIGA_OK;  // the dense path needs no workspace
+  if (ops & GIGA_OP_BWD_FILTER) *bytes = dw_filter_ws(desc);
+  return GIGA_OK;
+}
+
+giga_status_t giga_conv2d_fwd(const giga_conv2d_desc_t* desc, const void* x, const void* w,
+                              void* y, void* ws, size_t ws_bytes, void* stream) {
+  clear_error();
+  giga_status_t s = check_desc(desc);
+  if (s != GIGA_OK) return s;
+  (void)ws;
+  (void)ws_bytes;
+  if (!is_depthwise(desc)) return fail(GIGA_ERR_UNSUPPORTED, "dense filtering is not built");
+  const size_t es = elem_size(desc->dtype);
+  const size_t n = (size_t)dw_numel(desc);
+  if ((s = check_ptr(x, n, es, "x")) || (s = check_ptr(y, n, es, "y")) ||
+      (s = check_ptr(w, n ? (size_t)desc->C_in * desc->K * desc->K : 0, 4, "w")))
+    return s;
+  if (overlap(x, y, n * es)) return fail(GIGA_ERR_INVALID_ARG, "y aliases x");
+  if (n == 0) return GIGA_OK;
+  DwArgs a = make_args(desc);
+  a.x = x;
+  a.y = y;
+  a.w = static_cast<const float*>(w);
+  a.vec = vec_ok(a, x, y, nullptr);
+  return run_tuned(TUNE_FWD, a, static_cast<cudaStream_t>(stream));
+}
+
+giga_status_t giga_conv2d_bwd_input(const giga_conv2d_desc_t* desc, const void* dy,
+                                    const void* w, void* dx, void* ws, size_t ws_bytes,
+                                    void* stream) {
+  clear_error();
+  giga_status_t s = check_desc(desc);
+  if (s != GIGA_OK) return s;
+  (void)ws;
+  (void)ws_bytes;
+  if (!is_depthwise(desc)) return fail(GIGA_ERR_UNSUPPORTED, "dense filtering is not built");
+  const size_t es = elem_size(desc->dtype);
+  const size_t n = (size_t)dw_numel(desc);
+  if ((s = check_ptr(dy, n, es, "dy")) || (s = check_ptr(dx, n, es, "dx")) ||
+      (s = check_ptr(w, n ? (size_t)desc->C_in * desc->K * desc->K : 0, 4, "w")))
+    return s;
+  if (overlap(dy, dx, n * es)) return fail(GIGA_ERR_INVALID_ARG, "dx aliases dy");
+  if (n == 0) return GIGA_OK;
+  DwArgs a = make_args(desc);
+  a.dy = dy;
+  a.dx = dx;
+  a.w = static_cast<const float*>(w);
+  a.vec = vec_ok(a, dy, dx, nullptr);
+  return run_tuned(TUNE_BWD_INPUT, a, static_cast<cudaStream_t>(stream));
+}
+
+static giga_status_t bwd_common(const giga_conv2d_desc_t* desc, const void* x, const void* dy,
+                                const float* w, void* dx, float* dw, void* ws, size_t ws_bytes,
+                                void* stream, bool fused) {
+  giga_status_t s = check_desc(desc);
+  if (s != GIGA_OK) return s;
+  if (!is_depthwise(desc)) return fail(GIGA_ERR_UNSUPPORTED, "dense filtering is not built");
+  if (desc->K > kMaxKFilter)
+    return fail(GIGA_ERR_UNSUPPORTED, "the filter gradient supports K <= 15");
+  const size_t es = elem_size(desc->dtype);
+  const size_t n = (size_t)dw_numel(desc);
+  const size_t nw = (size_t)desc->C_in * desc->K * desc->K;
+  if ((s = check_ptr(x, n, es, "x")) || (s = check_ptr(dy, n, es, "dy")) ||
+      (s = check_ptr(dw, nw, 4, "dw")))
+    return s;
+  if (fused && ((s = check_ptr(dx, n, es, "dx")) || (s = check_ptr(w, n ? nw : 0, 4, "w"))))
+    return s;
+  if (fused && (overlap(dx, dy, n * es) || overlap(dx, x, n * es)))
+    return fail(GIGA_ERR_INVALID_ARG, "dx aliases an input");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (n == 0) {
+    if (nw) {
+      cudaError_t e = cudaMemsetAsync(dw, 0, nw * sizeof(float), st);
+      if (e != cudaSuccess) return cuda_fail(e, "zeroing dw");
+    }
+    return GIGA_OK;
+  }
+  if ((s = check_ws(ws, ws_bytes, dw_filter_ws(desc)))) return s;
+  DwArgs a = make_args(desc);
+  a.x = x;
+  a.dy = dy;
+  a.dx = dx;
+  a.w = w;
+  a.dw = dw;
+  a.partials = static_cast<float*>(ws);
+  a.vec = vec_ok(a, x, dy, fused ? dx : nullptr);
+  return run_tuned(fused ? TUNE_BWD_FUSED : TUNE_BWD_FILTER, a, st);
+}
+
+giga_status_t giga_conv2d_bwd_filter(const giga_conv2d_desc_t* desc, const void* x,
+                                     const void* dy, float* dw, void* ws, size_t ws_bytes,
+                                     void* stream) {
+  clear_error();
+  return bwd_common(desc, x, dy, nullptr, nullptr, dw, ws, ws_bytes, stream, false);
+}
+
+giga_status_t giga_conv2d_bwd(const giga_conv2d_desc_t* desc, const void* x, const void* dy,
+                              const float* w, void* dx, float* dw, void* ws, size_t ws_bytes,
+                              void* stream) {
+  clear_error();
+  return bwd_common(desc, x, dy, w, dx, dw, ws, ws_bytes, stream, true);
+}
+
+static int tune_op_of(int32_t op) {
+  switch (op) {
+    case GIGA_OP_FWD: return TUNE_FWD;
+    case GIGA_OP_BWD_INPUT: return TUNE_BWD_INPUT;
+    case GIGA_OP_BWD_FILTER: return TUNE_BWD_FILTER;
+    case GIGA_OP_BWD_INPUT | GIGA_OP_BWD_FILTER: return TUNE_BWD_FUSED;
+    default: return -1;
+  }
+}
+
+giga_status_t giga_autotune_conv2d(const giga_conv2d_desc_t* desc, int32_t ops, const void* x,
+                                   const void* w, void* y, const void* dy, void* dx, float* dw,
+                                   void* ws, size_t ws_bytes, void* stream) {
+  clear_error();
+  giga_status_t s = check_desc(desc);
+  if (s != GIGA_OK) return s;
+  if (!is_depthwise(desc)) return fail(GIGA_ERR_UNSUPPORTED, "only depthwise problems are tuned");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (stream_capturing(st)) return fail(GIGA_ERR_UNSUPPORTED, "cannot autotune while capturing");
+  if (dw_numel(desc) == 0) return GIGA_OK;
+  // Validate every requested op exactly like its entry point (one run each).
+  if ((ops & GIGA_OP_FWD) && (s = giga_conv2d_fwd(desc, x, w, y, ws, ws_bytes, stream))) return s;
+  const bool fused = (ops & GIGA_OP_BWD_INPUT) && (ops & GIGA_OP_BWD_FILTER);
+  if (fused) {
+    if ((s = giga_conv2d_bwd(desc, x, dy, static_cast<const float*>(w), dx, dw, ws, ws_bytes, stream)))
+      return s;
+  } else {
+    if ((ops & GIGA_OP_BWD_INPUT) && (s = giga_conv2d_bwd_input(desc, dy, w, dx, ws, ws_bytes, stream)))
+      return s;
+    if ((ops & GIGA_OP_BWD_FILTER) &&
+        (s = giga_conv2d_bwd_filter(desc, x, dy, dw, ws, ws_bytes, stream)))
+      return s;
+  }
+  DwArgs a = make_args(desc);
+  a.x = x; a.y = y; a.dy = dy; a.dx = dx; a.w = static_cast<const float*>(w); a.dw = dw;
+  a.partials = static_cast<float*>(ws);
+  a.vec = vec_ok(a, x, y, nullptr) && vec_ok(a, dy, dx, nullptr);
+  if ((ops & GIGA_OP_FWD) && (s = tune_dw_op(TUNE_FWD, a, st))) return s;
+  if (fused) return tune_dw_op(TUNE_BWD_FUSED, a, st);
+  if ((ops & GIGA_OP_BWD_INPUT) && (s = tune_dw_op(TUNE_BWD_INPUT, a, st))) return s;
+  if ((ops & GIGA_OP_BWD_FILTER) && (s = tune_dw_op(TUNE_BWD_FILTER, a, st))) return s;
+  return GIGA_OK;
+}
+
+int32_t giga_autotune_choice(const giga_conv2d_desc_t* desc, int32_t op) {
+  clear_error();
+  if (check_desc(desc) != GIGA_OK || !is_depthwise(desc)) return -1;
+  const int top = tune_op_of(op);
+  if (top < 0) return -1;
+  if (tune_mode() == 0) return 0;
+  const int id = tune_lookup(top, make_args(desc));
+  return id < 0 ? 0 : id;
+}
+
+const char* giga_status_string(giga_status_t status) {
+  switch (status) {
+    case GIGA_OK: return "success";
+    case GIGA_ERR_INVALID_ARG: return "invalid argument";
+    case GIGA_ERR_UNSUPPORTED: return "unsupported configuration";
+    case GIGA_ERR_MISALIGNED: return "misaligned pointer";
+    case GIGA_ERR_WORKSPACE: return "workspace missing, too small or misaligned";
+    case GIGA_ERR_CUDA: return "CUDA error";
+    case GIGA_ERR_TIMEOUT: return "device wait timed out";
+    default: return "unknown status";
+  }
+}
+
+const char* giga_last_error_detail(void) { return t_error.c_str(); }
+
+uint64_t giga_launch_count(void) { return t_launches; }
+
+void giga_launch_count_reset(void) { t_launches = 0; }
+
+}  // extern "C"

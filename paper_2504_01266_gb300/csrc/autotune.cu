@@ -1,0 +1,229 @@
+// autotune.cu -- picks the launch configuration of the depthwise kernels per
+// problem class by timing every candidate with CUDA events, and keeps the
+// choices in memory and (optionally) in a JSON file.
+//
+// Candidates:
+//   forward / input gradient: output rows per thread 8 (64 x 128 tiles) or
+//                             4 (32 x 128 tiles: twice the CTAs, less halo reuse);
+//   filter gradient (alone or fused): tiles per CTA = automatic, 2, 4, 8, 16
+//                             (fewer partial sums vs. better load balance).
+// Problem class: (op, dtype, K, border, floor(log2(N*C*H*W))).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <fstream>
+#include <map>
+#include <mutex>
+#include <sstream>
+#include <string>
+
+#include "dw_launch.h"
+#include "internal.h"
+
+namespace giga {
+
+static std::mutex g_mu;
+static std::map<std::string, int> g_cache;
+static int g_mode = -1;
+static bool g_loaded = false;
+
+static int env_mode() {
+  const char* e = std::getenv("GIGA_AUTOTUNE");
+  if (!e) return 1;
+  if (!std::strcmp(e, "off") || !std::strcmp(e, "0")) return 0;
+  if (!std::strcmp(e, "full") || !std::strcmp(e, "2")) return 2;
+  return 1;
+}
+
+int tune_mode() {
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (g_mode < 0) g_mode = env_mode();
+  return g_mode;
+}
+
+int tune_candidates(int op) { return (op == TUNE_FWD || op == TUNE_BWD_INPUT) ? 2 : 5; }
+
+static int auto_tiles_per_cta(const DwArgs& a) {
+  const int64_t tiles = a.N * a.C * (int64_t)((a.W + kTileW - 1) / kTileW) *
+                        (int64_t)((a.H + 63) / 64);
+  int64_t t = tiles / ((int64_t)sm_count() * 16);
+  if (t < 1) t = 1;
+  if (t > 16) t = 16;
+  return (int)t;
+}
+
+DwConfig tune_config(int op, int id, const DwArgs& a) {
+  DwConfig c;
+  c.rows_per_thread = 8;
+  c.tiles_per_cta = auto_tiles_per_cta(a);
+  if (op == TUNE_FWD || op == TUNE_BWD_INPUT) {
+    c.rows_per_thread = id == 1 ? 4 : 8;
+  } else {
+    static const int tpc[5] = {0, 2, 4, 8, 16};
+    if (id >= 1 && id <= 4) c.tiles_per_cta = tpc[id];
+  }
+  return c;
+}
+
+static std::string key_of(int op, const DwArgs& a) {
+  const double n = (double)a.N * a.C * a.H * a.W;
+  const int sc = n > 0 ? (int)std::floor(std::log2(n)) : 0;
+  char buf[96];
+  std::snprintf(buf, sizeof(buf), "%d:%d:%d:%d:%d", op, a.dtype, a.K, a.border, sc);
+  return buf;
+}
+
+// ---- JSON persistence: {"giga_autotune": 1, "entries": {"key": id, ...}}
+static bool parse_cache(const std::string& text, std::map<std::string, int>& out) {
+  if (text.find("\"giga_autotune\"") == std::string::npos) return false;
+  size_t p = text.find("\"entries\"");
+  if (p == std::string::npos) return false;
+  p = text.find('{', p);
+  if (p == std::string::npos) return false;
+  const size_t end = text.find('}', p);
+  if (end == std::string::npos) return false;
+  std::map<std::string, int> tmp;
+  while (true) {
+    size_t q0 = text.find('"', p);
+    if (q0 == std::string::npos || q0 > end) break;
+    size_t q1 = text.find('"', q0 + 1);
+    if (q1 == std::string::npos || q1 > end) return false;
+    std::string key = text.substr(q0 + 1, q1 - q0 - 1);
+    size_t colon = text.find(':', q1);
+    if (colon == std::string::npos || colon > end) return false;
+    char* stop = nullptr;
+    long v = std::strtol(text.c_str() + colon + 1, &stop, 10);
+    if (stop == text.c_str() + colon + 1 || v < 0 || v > 64) return false;
+    for (char ch : key)
+      if (!(ch == ':' || ch == '-' || (ch >= '0' && ch <= '9'))) return false;
+    tmp[key] = (int)v;
+    p = (size_t)(stop - text.c_str());
+  }
+  out.swap(tmp);
+  return true;
+}
+
+static bool load_file(const char* path) {
+  std::ifstream f(path);
+  if (!f) return false;
+  std::stringstream ss;
+  ss << f.rdbuf();
+  std::map<std::string, int> m;
+  if (!parse_cache(ss.str(), m)) return false;  // a corrupt cache is ignored
+  for (auto& kv : m) g_cache[kv.first] = kv.second;
+  return true;
+}
+
+static bool save_file(const char* path) {
+  std::string tmp = std::string(path) + ".tmp";
+  {
+    std::ofstream f(tmp);
+    if (!f) return false;
+    f << "{\"giga_autotune\": 1, \"entries\": {";
+    bool first = true;
+    for (auto& kv : g_cache) {
+      f << (first ? "" : ", ") << '"' << kv.first << "\": " << kv.second;
+      first = false;
+    }
+    f << "}}\n";
+  }
+  return std::rename(tmp.c_str(), path) == 0;
+}
+
+static void ensure_loaded() {
+  if (g_loaded) return;
+  g_loaded = true;
+  if (const char* p = std::getenv("GIGA_AUTOTUNE_CACHE")) load_file(p);
+}
+
+int tune_lookup(int op, const DwArgs& a) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  ensure_loaded();
+  auto it = g_cache.find(key_of(op, a));
+  if (it == g_cache.end()) return -1;
+  return it->second < tune_candidates(op) ? it->second : -1;
+}
+
+void tune_store(int op, const DwArgs& a, int id) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  ensure_loaded();
+  g_cache[key_of(op, a)] = id;
+  if (const char* p = std::getenv("GIGA_AUTOTUNE_CACHE")) save_file(p);
+}
+
+giga_status_t tune_dw_op(int op, const DwArgs& a, cudaStream_t st) {
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return fail(GIGA_ERR_CUDA, "event create");
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return fail(GIGA_ERR_CUDA, "event create");
+  }
+  int best = 0;
+  float best_ms = 1e30f;
+  giga_status_t status = GIGA_OK;
+  for (int id = 0; id < tune_candidates(op) && status == GIGA_OK; ++id) {
+    const DwConfig cfg = tune_config(op, id, a);
+    status = run_dw_op(op, a, cfg, st);  // warm-up
+    if (status != GIGA_OK) break;
+    cudaEventRecord(e0, st);
+    for (int rep = 0; rep < 3 && status == GIGA_OK; ++rep) status = run_dw_op(op, a, cfg, st);
+    cudaEventRecord(e1, st);
+    cudaError_t e = cudaEventSynchronize(e1);
+    if (e != cudaSuccess) {
+      status = cuda_fail(e, "autotune timing");
+      break;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = id;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (status == GIGA_OK) tune_store(op, a, best);
+  return status;
+}
+
+}  // namespace giga
+
+using namespace giga;
+
+extern "C" {
+
+giga_status_t giga_autotune_set_mode(int32_t mode) {
+  clear_error();
+  if (mode < 0 || mode > 2) return fail(GIGA_ERR_INVALID_ARG, "autotune mode must be 0, 1 or 2");
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_mode = mode;
+  return GIGA_OK;
+}
+
+int32_t giga_autotune_get_mode(void) { return tune_mode(); }
+
+giga_status_t giga_autotune_save(const char* path) {
+  clear_error();
+  if (!path) return fail(GIGA_ERR_INVALID_ARG, "path is NULL");
+  std::lock_guard<std::mutex> lk(g_mu);
+  return save_file(path) ? GIGA_OK : fail(GIGA_ERR_INVALID_ARG, "cannot write autotune cache");
+}
+
+giga_status_t giga_autotune_load(const char* path) {
+  clear_error();
+  if (!path) return fail(GIGA_ERR_INVALID_ARG, "path is NULL");
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_loaded = true;
+  return load_file(path) ? GIGA_OK
+                         : fail(GIGA_ERR_INVALID_ARG, "autotune cache missing or corrupt (ignored)");
+}
+
+void giga_autotune_clear(void) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_cache.clear();
+}
+
+}  // extern "C"

@@ -1,0 +1,50 @@
+// dw_launch.h -- host-side entry points of the depthwise kernels (one explicit
+// instantiation per filter size lives in dw_kNN.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace giga {
+
+constexpr int kMaxK = 31;        // forward / input gradient
+constexpr int kMaxKFilter = 15;  // filter gradient and the batched path
+
+// Forward (input_grad = false): y = K_w x with the border of `a`.
+// Input gradient (input_grad = true): dx = g from dy (flipped filter, zero
+// border); the clamp edge fold is a separate launch (dw_fixup_launch).
+template <int K>
+cudaError_t dw_fwd_launch(const DwArgs& a, const DwConfig& cfg, bool input_grad,
+                          cudaStream_t st);
+
+// Backward tile pass: mode 0 = fused g + filter partials, mode 1 = filter
+// partials only.  Writes partials[planes * chunks][K*K].
+template <int K>
+cudaError_t dw_bwd_launch(const DwArgs& a, const DwConfig& cfg, int mode, cudaStream_t st);
+
+// Number of CTAs per plane the backward pass uses for `tiles_per_cta`.
+int64_t dw_bwd_chunks_per_plane(int64_t H, int64_t W, int tiles_per_cta);
+
+// Clamp border: overwrite the edge pixels of dx with the exact adjoint.
+cudaError_t dw_fixup_launch(const DwArgs& a, cudaStream_t st);
+
+// dw[c][k] = sum over (n, chunk) of partials, in FP64, fixed order.
+cudaError_t dw_finalize_launch(const DwArgs& a, int64_t chunks_per_plane, cudaStream_t st);
+
+#define GIGA_DW_EXTERN(K)                                                                  \
+  extern template cudaError_t dw_fwd_launch<K>(const DwArgs&, const DwConfig&, bool,      \
+                                               cudaStream_t);
+#define GIGA_DW_EXTERN_BWD(K)                                                              \
+  extern template cudaError_t dw_bwd_launch<K>(const DwArgs&, const DwConfig&, int,       \
+                                               cudaStream_t);
+GIGA_DW_EXTERN(1) GIGA_DW_EXTERN(3) GIGA_DW_EXTERN(5) GIGA_DW_EXTERN(7)
+GIGA_DW_EXTERN(9) GIGA_DW_EXTERN(11) GIGA_DW_EXTERN(13) GIGA_DW_EXTERN(15)
+GIGA_DW_EXTERN(17) GIGA_DW_EXTERN(19) GIGA_DW_EXTERN(21) GIGA_DW_EXTERN(23)
+GIGA_DW_EXTERN(25) GIGA_DW_EXTERN(27) GIGA_DW_EXTERN(29) GIGA_DW_EXTERN(31)
+GIGA_DW_EXTERN_BWD(1) GIGA_DW_EXTERN_BWD(3) GIGA_DW_EXTERN_BWD(5) GIGA_DW_EXTERN_BWD(7)
+GIGA_DW_EXTERN_BWD(9) GIGA_DW_EXTERN_BWD(11) GIGA_DW_EXTERN_BWD(13) GIGA_DW_EXTERN_BWD(15)
+#undef GIGA_DW_EXTERN
+#undef GIGA_DW_EXTERN_BWD
+
+}  // namespace giga

@@ -1,0 +1,80 @@
+// dw_launch_impl.cuh -- launcher templates for the depthwise kernels; included
+// only by the per-filter-size translation units dw_kNN.cu.
+#pragma once
+
+#include "dw_kernels.cuh"
+#include "dw_launch.h"
+
+namespace giga {
+
+template <typename T, int K, int PY>
+static cudaError_t fwd_impl(const DwArgs& a, bool input_grad, cudaStream_t st) {
+  using G = Geo<K>;
+  constexpr int TH = kWarps * PY;
+  const size_t smem = sizeof(float) * (G::WPAD + (size_t)(TH + 2 * G::R) * G::SP);
+  auto kern = dw_fwd_kernel<T, K, PY>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  const int64_t tiles_x = (a.W + kTileW - 1) / kTileW;
+  const int64_t tiles_y = (a.H + TH - 1) / TH;
+  const int64_t grid = a.N * a.C * tiles_x * tiles_y;
+  const T* in = static_cast<const T*>(input_grad ? a.dy : a.x);
+  T* out = static_cast<T*>(input_grad ? a.dx : a.y);
+  kern<<<(unsigned)grid, kThreads, smem, st>>>(in, a.w, out, (int)a.C, (int)a.H, (int)a.W,
+                                               (int)tiles_x, (int)tiles_y,
+                                               input_grad ? 0 : a.border, a.vec,
+                                               input_grad ? 1 : 0);
+  note_launch();
+  return cudaGetLastError();
+}
+
+template <int K>
+cudaError_t dw_fwd_launch(const DwArgs& a, const DwConfig& cfg, bool input_grad,
+                          cudaStream_t st) {
+  const bool py4 = cfg.rows_per_thread == 4;
+  if (a.dtype == 0)
+    return py4 ? fwd_impl<float, K, 4>(a, input_grad, st) : fwd_impl<float, K, 8>(a, input_grad, st);
+  return py4 ? fwd_impl<__nv_bfloat16, K, 4>(a, input_grad, st)
+             : fwd_impl<__nv_bfloat16, K, 8>(a, input_grad, st);
+}
+
+template <typename T, int K, int MODE>
+static cudaError_t bwd_impl(const DwArgs& a, const DwConfig& cfg, cudaStream_t st) {
+  using S = BwdShape<K, MODE>;
+  const size_t smem = sizeof(float) * (size_t)S::SM_FLOATS;
+  auto kern = dw_bwd_kernel<T, K, MODE>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  const int64_t tiles_x = (a.W + kTileW - 1) / kTileW;
+  const int64_t tiles_y = (a.H + kBwdTileH - 1) / kBwdTileH;
+  const int64_t tpp = tiles_x * tiles_y;
+  const int64_t chunks = dw_bwd_chunks_per_plane(a.H, a.W, cfg.tiles_per_cta);
+  const int64_t grid = a.N * a.C * chunks;
+  kern<<<(unsigned)grid, kThreads, smem, st>>>(
+      static_cast<const T*>(a.x), static_cast<const T*>(a.dy), a.w, static_cast<T*>(a.dx),
+      a.partials, (int)a.C, (int)a.H, (int)a.W, (int)tiles_x, (int)tpp, (int)chunks,
+      cfg.tiles_per_cta, a.border, a.vec);
+  note_launch();
+  return cudaGetLastError();
+}
+
+template <int K>
+cudaError_t dw_bwd_launch(const DwArgs& a, const DwConfig& cfg, int mode, cudaStream_t st) {
+  if constexpr (K > kMaxKFilter) {
+    return cudaErrorInvalidValue;
+  } else {
+    if (a.dtype == 0)
+      return mode == 0 ? bwd_impl<float, K, 0>(a, cfg, st) : bwd_impl<float, K, 1>(a, cfg, st);
+    return mode == 0 ? bwd_impl<__nv_bfloat16, K, 0>(a, cfg, st)
+                     : bwd_impl<__nv_bfloat16, K, 1>(a, cfg, st);
+  }
+}
+
+#define GIGA_DW_INSTANTIATE(K)                                                            \
+  template cudaError_t dw_fwd_launch<K>(const DwArgs&, const DwConfig&, bool, cudaStream_t);
+#define GIGA_DW_INSTANTIATE_BWD(K)                                                        \
+  template cudaError_t dw_bwd_launch<K>(const DwArgs&, const DwConfig&, int, cudaStream_t);
+
+}  // namespace giga

@@ -1,0 +1,33 @@
+// internal.h -- host-side helpers shared by the C ABI translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "../../include/giga.h"
+#include "common.cuh"
+
+namespace giga {
+
+// Thread-local error detail; returns `status` for convenient `return fail(...)`.
+giga_status_t fail(giga_status_t status, const std::string& detail);
+giga_status_t cuda_fail(cudaError_t e, const char* where);
+void clear_error();
+
+int sm_count();  // multiprocessors of the current device (cached per device)
+
+// Autotuner (autotune.cu).
+enum TuneOp { TUNE_FWD = 0, TUNE_BWD_INPUT = 1, TUNE_BWD_FILTER = 2, TUNE_BWD_FUSED = 3 };
+int tune_mode();
+int tune_candidates(int op);
+DwConfig tune_config(int op, int id, const DwArgs& a);
+// Cached choice for (op, problem class); -1 if none.
+int tune_lookup(int op, const DwArgs& a);
+void tune_store(int op, const DwArgs& a, int id);
+// Run one depthwise op with candidate `id` (used by the autotuner).
+giga_status_t run_dw_op(int op, const DwArgs& a, const DwConfig& cfg, cudaStream_t st);
+// Benchmark all candidates of `op` on these buffers and store the fastest.
+giga_status_t tune_dw_op(int op, const DwArgs& a, cudaStream_t st);
+
+}  // namespace giga

@@ -1,0 +1,156 @@
+"""GPU parity of the depthwise path against the FP64 oracle, through the C ABI.
+
+Small cases span several tiles and ragged tails (H, W not multiples of the
+64 x 128 tile, W not a multiple of 4, images smaller than the filter); the
+full-size workloads are checked on sampled outputs and on every kind of
+border pixel.  Outputs are poisoned with NaN first, so unwritten elements fail.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads
+from helpers import (BF16_E2E_TOL, BF16_KERNEL_TOL, FP32_TOL, assert_fp32, normwise,
+                     poison_like, to_np)
+
+pytestmark = pytest.mark.gpu
+
+BORDER = {"zero": oracle.ZERO, "clamp": oracle.CLAMP}
+SHAPES = [(2, 3, 67, 131), (1, 2, 130, 260), (1, 1, 8, 8), (1, 2, 5, 7), (1, 1, 1, 1),
+          (2, 1, 3, 250), (1, 3, 200, 13)]
+KS = [1, 3, 5, 7, 9, 11, 13, 15]
+
+
+@pytest.fixture(scope="module")
+def giga():
+    import paper_2504_01266_gb300 as g
+    from paper_2504_01266_gb300 import build
+    build.build()
+    return g
+
+
+def make(shape, K, seed, dtype=torch.float32):
+    gen = torch.Generator().manual_seed(seed)
+    x = torch.rand(shape, generator=gen)
+    w = torch.randn((shape[1], K, K), generator=gen) * 0.1
+    dy = torch.randn(shape, generator=gen)
+    return x.to(dtype), w, dy.to(dtype)
+
+
+@pytest.mark.parametrize("K", KS + [17, 31])
+@pytest.mark.parametrize("border", ["zero", "clamp"])
+def test_fwd_fp32(giga, K, border):
+    for s, shape in enumerate(SHAPES):
+        x, w, _ = make(shape, K, 100 * K + s)
+        y = poison_like(x.cuda())
+        giga.conv2d_fwd(x.cuda(), w.cuda(), border, out=y)
+        b = BORDER[border]
+        ref = oracle.dw_fwd(x.numpy(), w.numpy(), b)
+        mag = oracle.dw_fwd(np.abs(x.numpy()), np.abs(w.numpy()), b)
+        assert_fp32(to_np(y), ref, mag, K * K, (shape, K, border))
+
+
+@pytest.mark.parametrize("K", [1, 3, 7, 15, 31])
+@pytest.mark.parametrize("border", ["zero", "clamp"])
+def test_bwd_input_fp32(giga, K, border):
+    for s, shape in enumerate(SHAPES):
+        _, w, dy = make(shape, K, 200 * K + s)
+        dx = poison_like(dy.cuda())
+        giga.conv2d_bwd_input(dy.cuda(), w.cuda(), border, out=dx)
+        b = BORDER[border]
+        ref = oracle.dw_bwd_input(dy.numpy(), w.numpy(), b)
+        mag = oracle.dw_bwd_input(np.abs(dy.numpy()), np.abs(w.numpy()), b)
+        # an edge pixel of the clamp fold sums up to (r + 1)^2 K^2 terms
+        assert_fp32(to_np(dx), ref, mag, (K // 2 + 1) ** 2 * K * K, (shape, K, border))
+
+
+@pytest.mark.parametrize("K", KS)
+@pytest.mark.parametrize("border", ["zero", "clamp"])
+def test_bwd_fused_and_filter_fp32(giga, K, border):
+    for s, shape in enumerate(SHAPES):
+        x, w, dy = make(shape, K, 300 * K + s)
+        xc, wc, dyc = x.cuda(), w.cuda(), dy.cuda()
+        dx, dw = giga.conv2d_bwd(xc, dyc, wc, border, dx=poison_like(dyc),
+                                 dw=torch.full((shape[1], K, K), float("nan"), device="cuda"))
+        dw_only = giga.conv2d_bwd_filter(xc, dyc, K, border)
+        b = BORDER[border]
+        ax, aw, ady = np.abs(x.numpy()), np.abs(w.numpy()), np.abs(dy.numpy())
+        ref_dx = oracle.dw_bwd_input(dy.numpy(), w.numpy(), b)
+        ref_dw = oracle.dw_bwd_filter(x.numpy(), dy.numpy(), K, b)
+        assert_fp32(to_np(dx), ref_dx, oracle.dw_bwd_input(ady, aw, b),
+                    (K // 2 + 1) ** 2 * K * K, (shape, K, border, "dx"))
+        # each filter tap sums N*H*W products; the FP32 part of the reduction
+        # sees at most that many terms, the cross-CTA part is FP64
+        mag_dw = oracle.dw_bwd_filter(ax, ady, K, b)
+        n = shape[0] * shape[2] * shape[3]
+        assert_fp32(to_np(dw), ref_dw, mag_dw, n, (shape, K, border, "dw"))
+        assert_fp32(to_np(dw_only), ref_dw, mag_dw, n, (shape, K, border, "dw only"))
+
+
+@pytest.mark.parametrize("K", [3, 9, 15])
+@pytest.mark.parametrize("border", ["zero", "clamp"])
+def test_bf16(giga, K, border):
+    shape = (2, 3, 67, 260)
+    x32, w, dy32 = make(shape, K, 400 + K)
+    xb, dyb = x32.to(torch.bfloat16), dy32.to(torch.bfloat16)
+    y = giga.conv2d_fwd(xb.cuda(), w.cuda(), border)
+    dx, dw = giga.conv2d_bwd(xb.cuda(), dyb.cuda(), w.cuda(), border)
+    b = BORDER[border]
+    xr, dyr = xb.float().numpy(), dyb.float().numpy()   # the BF16-rounded inputs
+    # (i) kernel error against the oracle on the rounded inputs
+    assert normwise(to_np(y), oracle.dw_fwd(xr, w.numpy(), b)) <= BF16_KERNEL_TOL
+    assert normwise(to_np(dx), oracle.dw_bwd_input(dyr, w.numpy(), b)) <= BF16_KERNEL_TOL
+    assert normwise(to_np(dw), oracle.dw_bwd_filter(xr, dyr, K, b)) <= FP32_TOL
+    # (ii) end to end against the oracle on the FP32 originals
+    assert normwise(to_np(y), oracle.dw_fwd(x32.numpy(), w.numpy(), b)) <= BF16_E2E_TOL
+    assert normwise(to_np(dx), oracle.dw_bwd_input(dy32.numpy(), w.numpy(), b)) <= BF16_E2E_TOL
+    assert normwise(to_np(dw), oracle.dw_bwd_filter(x32.numpy(), dy32.numpy(), K, b)) \
+        <= BF16_E2E_TOL
+
+
+def test_plain_small_gaussian(giga):
+    """512 x 512, one 5 x 5 normalised Gaussian (sigma 1), zero border: full compare."""
+    x, w = workloads.plain_small()
+    y = giga.conv2d_fwd(x.cuda(), w.cuda(), "zero")
+    ref = oracle.dw_fwd(x.numpy(), w.numpy(), oracle.ZERO)
+    assert normwise(to_np(y), ref) <= FP32_TOL
+
+
+def test_filter_gradient_is_deterministic(giga):
+    x, w, dy = make((4, 3, 300, 500), 7, 5)
+    xc, dyc = x.cuda(), dy.cuda()
+    a = giga.conv2d_bwd_filter(xc, dyc, 7, "clamp")
+    b = giga.conv2d_bwd_filter(xc, dyc, 7, "clamp")
+    assert torch.equal(a, b)
+
+
+def test_misaligned_view_uses_scalar_path(giga):
+    """A view starting one element in (not 16-byte aligned) takes the scalar
+    staging path and still matches."""
+    x, w, _ = make((1, 1, 40, 129), 5, 9)
+    base = torch.zeros(40 * 129 + 1).cuda()
+    base[1:] = x.reshape(-1).cuda()
+    xv = base[1:].view(1, 1, 40, 129)
+    y = giga.conv2d_fwd(xv, w.cuda(), "clamp")
+    assert normwise(to_np(y), oracle.dw_fwd(x.numpy(), w.numpy(), oracle.CLAMP)) <= FP32_TOL
+
+
+# ------------------------------------------------------- full-size workloads
+
+@pytest.mark.parametrize("K", [3, 7, 15])
+def test_plain_scale_sampled(giga, K):
+    """8 x 3 x 4096 x 4096 FP32, clamp border, in the benchmark's launch
+    configuration; sampled outputs and every kind of border pixel."""
+    x, w = workloads.plain_scale(K)
+    xc, wc = x.cuda(), w.cuda()
+    y = giga.conv2d_fwd(xc, wc, "clamp")
+    N, C, H, W = x.shape
+    idx = torch.cat([workloads.sample_indices(x.numel(), 3000, salt=K),
+                     workloads.border_indices(N, C, H, W, per_plane=2, salt=K)])
+    idx = torch.unique(idx)
+    got = y.reshape(-1)[idx.cuda()].double().cpu().numpy()
+    ref = oracle.dw_fwd_points(x.numpy(), w.numpy(), oracle.CLAMP, idx.numpy())
+    assert normwise(got, ref) <= FP32_TOL
+    del xc, y
+    torch.cuda.empty_cache()
