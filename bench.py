@@ -61,7 +61,7 @@ def taps_per_step():
 
 class ClockSampler:
     """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -74,7 +74,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -84,7 +84,11 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.time(), line.strip()))
+
+    def mark(self, start: float, end: float):
+        """Restrict the summary to samples taken in [start, end] (host time)."""
+        self.window = (start, end)
 
     def __exit__(self, *exc):
         if self.proc:
@@ -98,7 +102,10 @@ class ClockSampler:
     def summary(self):
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in self.lines:
+        lo, hi = getattr(self, "window", (0.0, float("inf")))
+        # a sample printed up to one period after the window still describes it
+        lines = [ln for t, ln in self.lines if lo <= t <= hi + 0.05]
+        for line in lines:
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 9:
                 continue
@@ -113,7 +120,7 @@ class ClockSampler:
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "period_ms": 50}
 
 
 # ------------------------------------------------------------- distributed
@@ -143,15 +150,15 @@ def barrier(world: int):
 
 # ------------------------------------------------------------- CPU oracle
 
-def oracle_sample_rate(rows: int = H):
+def oracle_sample_rate(rows: int = H, images: int = 1):
     """Time the FP64 oracle (fwd + input grad + filter grad for every K) on
     `rows` x 4096 pixels of one image's 3 channels (default: one whole image
     of the 8); returns (Gpixel*tap/s, threads, seconds, description)."""
     import numpy as np
     import oracle
     rng = np.random.default_rng(2504)
-    x = rng.random((1, C, rows, W))
-    dy = rng.standard_normal((1, C, rows, W))
+    x = rng.random((images, C, rows, W))
+    dy = rng.standard_normal((images, C, rows, W))
     taps = 0
     t0 = time.perf_counter()
     for K in KS:
@@ -159,9 +166,10 @@ def oracle_sample_rate(rows: int = H):
         oracle.dw_fwd(x, w, oracle.CLAMP)
         oracle.dw_bwd_input(dy, w, oracle.CLAMP)
         oracle.dw_bwd_filter(x, dy, K, oracle.CLAMP)
-        taps += 3 * C * rows * W * K * K
+        taps += 3 * images * C * rows * W * K * K
     dt = time.perf_counter() - t0
-    desc = f"1x{C}x{rows}x{W} band, fwd+bwd_input+bwd_filter for K in {list(KS)}, FP64"
+    desc = (f"{images}x{C}x{rows}x{W} of the {N}x{C}x{H}x{W} workload, "
+            f"fwd+bwd_input+bwd_filter for K in {list(KS)}, FP64")
     return taps / dt / 1e9, oracle.num_threads(), dt, desc
 
 
@@ -258,11 +266,14 @@ def run_giga(args):
     start = torch.cuda.Event(enable_timing=True)
     end = torch.cuda.Event(enable_timing=True)
     with ClockSampler(dev.index if dev.index is not None else 0) as clocks:
+        time.sleep(0.3)  # let the sampler start before the timed region
+        t_host0 = time.time()
         start.record(stream)
         for _ in range(args.steps):
             step(record=True)
         end.record(stream)
         torch.cuda.synchronize(dev)
+        clocks.mark(t_host0, time.time())
     launches = L.giga_launch_count()
     barrier(world)
     ms_local = start.elapsed_time(end) / args.steps
@@ -274,7 +285,9 @@ def run_giga(args):
     px = N * C * H * W
     ops = []
     for (K, op), evs in op_ms.items():
-        t = statistics.mean(a.elapsed_time(b) for a, b in evs) * 1e-3
+        # median over steps: the first op of the first step can include host
+        # launch latency (the stream is idle when the timed region starts)
+        t = statistics.median(a.elapsed_time(b) for a, b in evs) * 1e-3
         bytes_ = px * (8 if op == "fwd" else 12)
         fma = px * K * K * (1 if op == "fwd" else 2)
         t_hbm = bytes_ / (pk["hbm_gbs"] * 1e9)
@@ -333,7 +346,7 @@ def run_giga(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        v, cores, dt, desc = oracle_sample_rate()
+        v, cores, dt, desc = oracle_sample_rate(H, 2)
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{desc}; {dt:.1f} s"}
 

@@ -152,3 +152,58 @@ class DepthwiseConv2d(torch.autograd.Function):
 def conv2d(x: torch.Tensor, w: torch.Tensor, border="zero") -> torch.Tensor:
     """Depthwise K x K filtering with autograd support."""
     return DepthwiseConv2d.apply(x, w, border)
+
+
+# ------------------------------------------------------------ ragged batches
+
+class BatchedPlan:
+    """One persistent launch over a ragged list of images (giga_batched_plan_*).
+
+    ``images``: list of dicts with device tensors ``x`` / ``y`` / ``dy`` / ``dx``
+    of shape (C, H, W) (any subset the ops need) and ``w`` / ``dw`` of shape
+    (C, K, K) FP32.  ``ops`` is a GIGA_OP_* bitmask.  ``run()`` is capturable
+    into a CUDA graph once ``upload()`` has been issued.
+    """
+
+    def __init__(self, images, ops, border="zero", dtype=torch.float32):
+        self.n = len(images)
+        arr = (_lib.giga_image_t * max(1, self.n))()
+        self.keep = []
+        for i, im in enumerate(images):
+            ref = im.get("x") if im.get("x") is not None else im.get("dy")
+            C, H, W = ref.shape[-3:]
+            K = im["w"].shape[-1] if im.get("w") is not None else im["dw"].shape[-1]
+            _require_cuda(*[im.get(k) for k in ("x", "y", "dy", "dx", "w", "dw")])
+            arr[i] = _lib.giga_image_t(
+                _ptr(im.get("x")), _ptr(im.get("y")), _ptr(im.get("dy")), _ptr(im.get("dx")),
+                _ptr(im.get("w")), _ptr(im.get("dw")), H, W, C, K)
+            self.keep.append(im)
+        self.arr = arr
+        self.ops = ops
+        self.plan = _lib.giga_batched_plan_create(arr, self.n, ops, _border(border),
+                                                  DTYPES[dtype])
+        self.ws_bytes = _lib.giga_batched_plan_workspace_size(self.plan)
+        dev = ref.device if self.n else torch.device("cuda")
+        self.ws = torch.empty(max(self.ws_bytes, 256), dtype=torch.uint8, device=dev)
+        self.device = dev
+
+    def upload(self):
+        _lib.check(_lib.giga_batched_plan_upload(self.plan, self.ws.data_ptr(), self.ws.numel(),
+                                                 _stream(self.device)),
+                   "giga_batched_plan_upload")
+
+    def run(self):
+        _lib.check(_lib.giga_batched_plan_run(self.plan, self.ws.data_ptr(), self.ws.numel(),
+                                              _stream(self.device)),
+                   "giga_batched_plan_run")
+
+    def close(self):
+        if self.plan:
+            _lib.giga_batched_plan_destroy(self.plan)
+            self.plan = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 namespace giga {
 
 // Tile geometry of the depthwise kernels: a CTA of 8 warps owns a tile of
@@ -77,5 +79,20 @@ template <> struct Elem<__nv_bfloat16> {
 
 // Host-side launch accounting (giga_launch_count).
 void note_launch(int n = 1);
+
+// Raise a kernel's dynamic shared-memory limit once per device (the attribute
+// is per context; later calls are a bit test).  One flag word per kernel.
+template <auto kern>
+inline cudaError_t set_smem_once(size_t bytes) {
+  static std::atomic<uint64_t> done{0};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const uint64_t bit = 1ull << (dev & 63);
+  if (done.load(std::memory_order_acquire) & bit) return cudaSuccess;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) done.fetch_or(bit, std::memory_order_release);
+  return e;
+}
 
 }  // namespace giga

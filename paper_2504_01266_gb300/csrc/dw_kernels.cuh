@@ -61,13 +61,13 @@ __device__ __forceinline__ void cta_barrier() { asm volatile("bar.sync 0;" ::: "
 // Stage rows [ty0 - HR, ty0 - HR + rows) x cols [tx0 - HC, tx0 - HC + pitch)
 // of one image plane into shared memory as FP32.  Outside the image: zero, or
 // (clamp) the nearest edge pixel, row and column clamped independently.
-template <typename T, int HR, int HC, int PITCH>
+template <typename T, int HR, int HC, int PITCH, int NT = kThreads>
 __device__ __forceinline__ void stage_tile(float* __restrict__ sm, const T* __restrict__ plane,
                                            int H, int W, int ty0, int tx0, int rows,
                                            bool clamp, bool vec) {
   constexpr int CPR = PITCH / 4;
   const int total = rows * CPR;
-  for (int k = threadIdx.x; k < total; k += kThreads) {
+  for (int k = threadIdx.x; k < total; k += NT) {
     const int sr = k / CPR;
     const int sc = (k - sr * CPR) * 4;
     int gi = ty0 - HR + sr;

@@ -13,8 +13,7 @@ static cudaError_t fwd_impl(const DwArgs& a, bool input_grad, cudaStream_t st) {
   constexpr int TH = kWarps * PY;
   const size_t smem = sizeof(float) * (G::WPAD + (size_t)(TH + 2 * G::R) * G::SP);
   auto kern = dw_fwd_kernel<T, K, PY>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  cudaError_t e = set_smem_once<dw_fwd_kernel<T, K, PY>>(smem);
   if (e != cudaSuccess) return e;
   const int64_t tiles_x = (a.W + kTileW - 1) / kTileW;
   const int64_t tiles_y = (a.H + TH - 1) / TH;
@@ -44,8 +43,7 @@ static cudaError_t bwd_impl(const DwArgs& a, const DwConfig& cfg, cudaStream_t s
   using S = BwdShape<K, MODE>;
   const size_t smem = sizeof(float) * (size_t)S::SM_FLOATS;
   auto kern = dw_bwd_kernel<T, K, MODE>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  cudaError_t e = set_smem_once<dw_bwd_kernel<T, K, MODE>>(smem);
   if (e != cudaSuccess) return e;
   const int64_t tiles_x = (a.W + kTileW - 1) / kTileW;
   const int64_t tiles_y = (a.H + kBwdTileH - 1) / kBwdTileH;

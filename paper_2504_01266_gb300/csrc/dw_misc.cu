@@ -3,6 +3,7 @@
 //  * the FP64 fixed-order reduction of the per-CTA filter-gradient partials.
 #include <algorithm>
 
+#include "dw_fold.cuh"
 #include "dw_kernels.cuh"
 #include "dw_launch.h"
 
@@ -14,67 +15,23 @@ int64_t dw_bwd_chunks_per_plane(int64_t H, int64_t W, int tiles_per_cta) {
 }
 
 // ------------------------------------------------------------- edge fold
-// With the clamp border the forward pass reads x at B(i + a - r), B clamping
-// to [0, n).  Its adjoint returns w[a][b] * dy[i][j] to that clamped pixel, so
-// an edge pixel p of a row collects every (i, a) with B(i + a - r) = p:
-//   p = 0     : i + a - r <= 0,   p = n - 1 : i + a - r >= n - 1,
-//   otherwise : i + a - r == p    (both conditions when n == 1).
-// For each filter row a those i form one interval; this kernel evaluates
-//   dx[p][q] = sum_{a,b} w[a][b] * sum_{i in I(p,a)} sum_{j in J(q,b)} dy[i][j]
-// directly for the pixels of the first/last row and column of every plane and
-// overwrites what the tile pass wrote there.
-__device__ __forceinline__ void fold_interval(int p, int n, int a, int r, int& lo, int& hi) {
-  const int ulo = (p == 0) ? -(1 << 30) : p;
-  const int uhi = (p == n - 1) ? (1 << 30) : p;
-  lo = max(0, ulo - a + r);
-  hi = min(n - 1, uhi - a + r);
-}
-
 template <typename T>
 __global__ void dw_fixup_kernel(const T* __restrict__ dy, const float* __restrict__ w,
                                 T* __restrict__ dx, int C, int H, int W, int K,
                                 int64_t edge_per_plane, int64_t total) {
-  const int r = (K - 1) / 2;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t plane = e / edge_per_plane;
-    int64_t k = e - plane * edge_per_plane;
-    int p, q;
-    // enumerate: first row, last row, then first/last column of the inner rows
-    if (k < W) {
-      p = 0; q = (int)k;
-    } else if (H > 1 && k < 2 * (int64_t)W) {
-      p = H - 1; q = (int)(k - W);
-    } else {
-      k -= (H > 1 ? 2 * (int64_t)W : W);
-      p = 1 + (int)(k / (W > 1 ? 2 : 1));
-      q = (W > 1 && (k & 1)) ? W - 1 : 0;
-    }
-    const T* g = dy + plane * (int64_t)H * W;
-    const float* f = w + (int64_t)(plane % C) * K * K;
-    float sum = 0.f;
-    for (int a = 0; a < K; ++a) {
-      int ilo, ihi;
-      fold_interval(p, H, a, r, ilo, ihi);
-      if (ilo > ihi) continue;
-      for (int b = 0; b < K; ++b) {
-        int jlo, jhi;
-        fold_interval(q, W, b, r, jlo, jhi);
-        if (jlo > jhi) continue;
-        float s = 0.f;
-        for (int i = ilo; i <= ihi; ++i)
-          for (int j = jlo; j <= jhi; ++j) s += Elem<T>::load(g + (int64_t)i * W + j);
-        sum = fmaf(f[a * K + b], s, sum);
-      }
-    }
-    Elem<T>::store(dx + plane * (int64_t)H * W + (int64_t)p * W + q, sum);
+    const int64_t k = e - plane * edge_per_plane;
+    fold_edge_pixel<T>(dy + plane * (int64_t)H * W, w + (int64_t)(plane % C) * K * K,
+                       dx + plane * (int64_t)H * W, H, W, K, k);
   }
 }
 
 cudaError_t dw_fixup_launch(const DwArgs& a, cudaStream_t st) {
   if (a.border != 1 || a.N * a.C * a.H * a.W == 0) return cudaSuccess;
   const int64_t H = a.H, W = a.W;
-  int64_t edge = (H == 1 || W == 1) ? H * W : 2 * W + 2 * (H - 2);
+  const int64_t edge = edge_pixels(H, W);
   const int64_t total = a.N * a.C * edge;
   const int threads = 128;
   const int64_t blocks = std::min<int64_t>((total + threads - 1) / threads, 65535);
