@@ -108,6 +108,27 @@ giga_status_t giga_conv2d_bwd(const giga_conv2d_desc_t* desc, const void* x, con
                               const float* w, void* dx, float* dw, void* ws, size_t ws_bytes,
                               void* stream);
 
+/* Filter gradient for callers that cannot allocate device memory.  The paper
+ * has no counterpart: this serves code that runs under a fixed, pre-reserved
+ * memory budget, plugins whose host framework offers no workspace, and paths
+ * where cudaMalloc's implicit device synchronisation is not acceptable.
+ * Arguments and result are those of giga_conv2d_bwd_filter without the
+ * workspace: the per-CTA partial sums go to a scratch array inside the
+ * library, a 4 MiB __device__ array (1,048,576 FP32 partial sums) that every
+ * GPU which loads the library holds until the process exits.  The call itself
+ * allocates nothing.
+ *   - Limit: problems whose partial sums do not fit the array even with one
+ *     CTA per image plane (N*C*K*K > 1,048,576) return GIGA_ERR_INVALID_ARG
+ *     and say so in giga_last_error_detail(); use giga_conv2d_bwd_filter.
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress with that device current); make that first call
+ *     before any stream capture.
+ *   - All calls share the one array, which keeps the last call's contents
+ *     (nothing in it needs to start at zero).  Calls that overlap on the GPU --
+ *     different streams or host threads -- race on it; serialise them. */
+giga_status_t giga_conv2d_bwd_filter_noalloc(const giga_conv2d_desc_t* desc, const void* x,
+                                             const void* dy, float* dw, void* stream);
+
 /* ------------------------------------------------------------------------
  * Ragged batches (the paper's unfinished "database of images", Section 5):
  * images of different sizes, each with its own depthwise filters, processed

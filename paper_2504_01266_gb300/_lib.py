@@ -36,7 +36,8 @@ GIGA_OP_BWD_FILTER = 4
 # Every symbol include/giga.h declares (checked by the CPU tests).
 EXPORTS = (
     "giga_conv2d_workspace_size", "giga_conv2d_fwd", "giga_conv2d_bwd_input",
-    "giga_conv2d_bwd_filter", "giga_conv2d_bwd", "giga_batched_plan_create",
+    "giga_conv2d_bwd_filter", "giga_conv2d_bwd", "giga_conv2d_bwd_filter_noalloc",
+    "giga_batched_plan_create",
     "giga_batched_plan_workspace_size", "giga_batched_plan_upload", "giga_batched_plan_run",
     "giga_batched_plan_destroy", "giga_conv2d_batched", "giga_conv2d_batched_workspace_size",
     "giga_autotune_set_mode", "giga_autotune_get_mode", "giga_autotune_conv2d",
@@ -83,6 +84,7 @@ _SIGS = {
     "giga_conv2d_bwd_input": (_ST, [_DESC, _P, _P, _P, _P, _SZ, _P]),
     "giga_conv2d_bwd_filter": (_ST, [_DESC, _P, _P, _P, _P, _SZ, _P]),
     "giga_conv2d_bwd": (_ST, [_DESC, _P, _P, _P, _P, _P, _P, _SZ, _P]),
+    "giga_conv2d_bwd_filter_noalloc": (_ST, [_DESC, _P, _P, _P, _P]),
     "giga_batched_plan_create": (_ST, [_IMG, _I32, _I32, _I32, _I32, ctypes.POINTER(_P)]),
     "giga_batched_plan_workspace_size": (_ST, [_P, ctypes.POINTER(_SZ)]),
     "giga_batched_plan_upload": (_ST, [_P, _P, _SZ, _P]),
@@ -161,6 +163,10 @@ def giga_conv2d_bwd_input(d, dy, w, dx, ws, ws_bytes, stream) -> int:
 
 def giga_conv2d_bwd_filter(d, x, dy, dw, ws, ws_bytes, stream) -> int:
     return load().giga_conv2d_bwd_filter(ctypes.byref(d), x, dy, dw, ws, ws_bytes, stream)
+
+
+def giga_conv2d_bwd_filter_noalloc(d, x, dy, dw, stream) -> int:
+    return load().giga_conv2d_bwd_filter_noalloc(ctypes.byref(d), x, dy, dw, stream)
 
 
 def giga_conv2d_bwd(d, x, dy, w, dx, dw, ws, ws_bytes, stream) -> int:
