@@ -256,6 +256,19 @@ def run_giga(args):
                 op_ms[(K, "fwd")].append((e0, e1))
                 op_ms[(K, "bwd")].append((e1, e2))
 
+    # autotune every (K, op) on the real buffers once, outside the timed region
+    tuned = {}
+    if not args.no_tune:
+        for K in KS:
+            d = descs[K]
+            L.check(L.giga_autotune_conv2d(d, L.GIGA_OP_FWD | L.GIGA_OP_BWD_INPUT |
+                                           L.GIGA_OP_BWD_FILTER, x.data_ptr(),
+                                           filt[K].data_ptr(), y.data_ptr(), dy.data_ptr(),
+                                           dx.data_ptr(), dws[K].data_ptr(), ws.data_ptr(),
+                                           ws_bytes, sp), "autotune")
+            tuned[K] = {"fwd": L.giga_autotune_choice(d, L.GIGA_OP_FWD),
+                        "bwd": L.giga_autotune_choice(d, L.GIGA_OP_BWD_INPUT |
+                                                      L.GIGA_OP_BWD_FILTER)}
     for _ in range(max(args.warmup, 3)):
         step()
     torch.cuda.synchronize(dev)
@@ -358,7 +371,8 @@ def run_giga(args):
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "N": N, "C": C, "H": H, "W": W, "K": list(KS),
                        "border": "clamp", "parallelism": f"replicas{world}",
-                       "l2": "inputs larger than L2 (1.6 GB per tensor), no flush"},
+                       "l2": "inputs larger than L2 (1.6 GB per tensor), no flush",
+                       "autotune": tuned},
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,
@@ -381,6 +395,7 @@ def main():
     ap.add_argument("--impl", default="giga", choices=["giga", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="built-in default configurations")
     ap.add_argument("--images", type=int, default=N,
                     help="images per GPU (profiling runs use 1: 201 MB per tensor, above L2)")
     args = ap.parse_args()

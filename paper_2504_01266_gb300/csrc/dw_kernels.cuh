@@ -39,7 +39,8 @@ struct Geo {
   static constexpr int SP = kTileW + 2 * RP;        // staged row pitch (floats)
   static constexpr int OFF = RP - R;                // first column a lane needs
   static constexpr int NV = (OFF + K + 2) / 4 + 1;  // float4 loads per lane per row
-  static constexpr int WPAD = (K * K + 3) / 4 * 4;  // staged filter (floats)
+  static constexpr int KP = (K + 3) / 4 * 4;         // staged filter row pitch
+  static constexpr int WPAD = K * KP;               // staged filter (floats)
 };
 
 // Filter rows held in registers per pass of the forward-style loop.
@@ -58,32 +59,106 @@ constexpr int kBwdTileH = 64;
 
 __device__ __forceinline__ void cta_barrier() { asm volatile("bar.sync 0;" ::: "memory"); }
 
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// cp.async with zero fill: src_bytes = 0 writes zeros and reads nothing.
+__device__ __forceinline__ void cp_async16(float* dst, const void* src, bool valid) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_addr(dst)), "l"(src),
+               "r"(valid ? 16 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async4(float* dst, const void* src, bool valid) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_addr(dst)), "l"(src),
+               "r"(valid ? 4 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Wait for this thread's staging copies, then for the whole CTA.
+__device__ __forceinline__ void stage_wait() {
+  cp_async_wait_all();
+  cta_barrier();
+}
+
+// A 16-byte shared load the compiler may not re-issue: the value must stay
+// in registers (used for filter taps and dy blocks that feed many FMAs).
+__device__ __forceinline__ float4 lds128_pinned(const float* p) {
+  float4 v;
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "r"(smem_addr(p)));
+  return v;
+}
+
+// One staged chunk of 4 consecutive columns at (gi, gj..gj+3), border applied.
+template <typename T>
+__device__ __forceinline__ float4 load_chunk(const T* __restrict__ plane, int H, int W, int gi,
+                                             int gj, bool clamp, bool vec) {
+  float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+  bool row_ok = gi >= 0 && gi < H;
+  if (!row_ok && clamp) {
+    gi = gi < 0 ? 0 : H - 1;
+    row_ok = true;
+  }
+  if (row_ok) {
+    const T* src = plane + (int64_t)gi * W;
+    if (vec && gj >= 0 && gj + 3 < W) {
+      v = Elem<T>::load4(src + gj);
+    } else {
+      float e[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        int j = gj + q;
+        bool ok = j >= 0 && j < W;
+        if (!ok && clamp) {
+          j = j < 0 ? 0 : W - 1;
+          ok = true;
+        }
+        e[q] = ok ? Elem<T>::load(src + j) : 0.f;
+      }
+      v = make_float4(e[0], e[1], e[2], e[3]);
+    }
+  }
+  return v;
+}
+
 // Stage rows [ty0 - HR, ty0 - HR + rows) x cols [tx0 - HC, tx0 - HC + pitch)
 // of one image plane into shared memory as FP32.  Outside the image: zero, or
 // (clamp) the nearest edge pixel, row and column clamped independently.
+// FP32 storage: asynchronous cp.async copies (16 bytes where the chunk is
+// inside the image and aligned, 4 bytes otherwise; zero fill for the zero
+// border), so every copy of the tile is in flight at once.  BF16 storage:
+// 4 chunks per thread are loaded before any is stored (widened to FP32).
+// Completion: stage_wait().
 template <typename T, int HR, int HC, int PITCH, int NT = kThreads>
 __device__ __forceinline__ void stage_tile(float* __restrict__ sm, const T* __restrict__ plane,
                                            int H, int W, int ty0, int tx0, int rows,
                                            bool clamp, bool vec) {
   constexpr int CPR = PITCH / 4;
   const int total = rows * CPR;
-  for (int k = threadIdx.x; k < total; k += NT) {
-    const int sr = k / CPR;
-    const int sc = (k - sr * CPR) * 4;
-    int gi = ty0 - HR + sr;
-    const int gj = tx0 - HC + sc;
-    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-    bool row_ok = gi >= 0 && gi < H;
-    if (!row_ok && clamp) {
-      gi = gi < 0 ? 0 : H - 1;
-      row_ok = true;
-    }
-    if (row_ok) {
+  if constexpr (sizeof(T) == 4) {
+    for (int k = threadIdx.x; k < total; k += NT) {
+      const int sr = k / CPR;
+      const int sc = (k - sr * CPR) * 4;
+      int gi = ty0 - HR + sr;
+      const int gj = tx0 - HC + sc;
+      float* dst = sm + sr * PITCH + sc;
+      bool row_ok = gi >= 0 && gi < H;
+      if (!row_ok && clamp) {
+        gi = gi < 0 ? 0 : H - 1;
+        row_ok = true;
+      }
+      if (!row_ok) {
+        cp_async16(dst, plane, false);
+        continue;
+      }
       const T* src = plane + (int64_t)gi * W;
       if (vec && gj >= 0 && gj + 3 < W) {
-        v = Elem<T>::load4(src + gj);
+        cp_async16(dst, src + gj, true);
       } else {
-        float e[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           int j = gj + q;
@@ -92,12 +167,46 @@ __device__ __forceinline__ void stage_tile(float* __restrict__ sm, const T* __re
             j = j < 0 ? 0 : W - 1;
             ok = true;
           }
-          e[q] = ok ? Elem<T>::load(src + j) : 0.f;
+          cp_async4(dst + q, ok ? src + j : plane, ok);
         }
-        v = make_float4(e[0], e[1], e[2], e[3]);
       }
     }
-    *reinterpret_cast<float4*>(sm + sr * PITCH + sc) = v;
+    cp_async_commit();
+  } else {
+    constexpr int U = 4;
+    for (int k0 = threadIdx.x; k0 < total; k0 += U * NT) {
+      float4 v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int k = k0 + u * NT;
+        if (k < total) {
+          const int sr = k / CPR;
+          const int sc = (k - sr * CPR) * 4;
+          v[u] = load_chunk<T>(plane, H, W, ty0 - HR + sr, tx0 - HC + sc, clamp, vec);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int k = k0 + u * NT;
+        if (k < total) {
+          const int sr = k / CPR;
+          const int sc = (k - sr * CPR) * 4;
+          *reinterpret_cast<float4*>(sm + sr * PITCH + sc) = v[u];
+        }
+      }
+    }
+  }
+}
+
+// Stage a K x K filter with rows padded to KP (zeros), optionally rotated by
+// 180 degrees (the input gradient's flipped filter).
+template <int K>
+__device__ __forceinline__ void stage_filter(float* __restrict__ sm, const float* __restrict__ w,
+                                             bool flip, int NT) {
+  constexpr int KP = Geo<K>::KP;
+  for (int k = threadIdx.x; k < K * KP; k += NT) {
+    const int a = k / KP, b = k - (k / KP) * KP;
+    sm[k] = b < K ? w[flip ? (K - 1 - a) * K + (K - 1 - b) : a * K + b] : 0.f;
   }
 }
 
@@ -133,18 +242,24 @@ __device__ __forceinline__ void load_window_row(const float* __restrict__ row,
   }
 }
 
-// acc[py][px] += sum_{s < A, b < K} f[s*K + b] * win[(py + s) * SP + OFF + px + b]
+// acc[py][px] += sum_{s < A, b < K} f[s*KP + b] * win[(py + s) * SP + OFF + px + b]
 // `win` points at the staged row of output row 0 plus filter row 0 of this
 // group, at the lane's first column; `f` at filter row 0 of this group.
 template <int K, int PY, int A>
 __device__ __forceinline__ void fwd_group(const float* __restrict__ win,
                                           const float* __restrict__ f, float (&acc)[PY][4]) {
   using G = Geo<K>;
-  float wr[A][K];
+  float wr[A][G::KP];
 #pragma unroll
   for (int s = 0; s < A; ++s)
 #pragma unroll
-    for (int b = 0; b < K; ++b) wr[s][b] = f[s * K + b];
+    for (int b = 0; b < G::KP; b += 4) {
+      const float4 t = lds128_pinned(f + s * G::KP + b);
+      wr[s][b] = t.x;
+      wr[s][b + 1] = t.y;
+      wr[s][b + 2] = t.z;
+      wr[s][b + 3] = t.w;
+    }
 #pragma unroll
   for (int ir = 0; ir < PY + A - 1; ++ir) {
     float buf[4 * G::NV];
@@ -175,37 +290,38 @@ __device__ __forceinline__ void fwd_block(const float* __restrict__ win,
     for (int px = 0; px < 4; ++px) acc[py][px] = 0.f;
 #pragma unroll 1
   for (int g = 0; g < NG; ++g)
-    fwd_group<K, PY, A>(win + g * A * Geo<K>::SP, f + g * A * K, acc);
-  if constexpr (REM > 0) fwd_group<K, PY, REM>(win + NG * A * Geo<K>::SP, f + NG * A * K, acc);
+    fwd_group<K, PY, A>(win + g * A * Geo<K>::SP, f + g * A * Geo<K>::KP, acc);
+  if constexpr (REM > 0)
+    fwd_group<K, PY, REM>(win + NG * A * Geo<K>::SP, f + NG * A * Geo<K>::KP, acc);
 }
 
-// Filter gradient of one 8-row dy block for the filter rows [a_lo, a_lo + nrows):
+// Filter gradient of one DR-row dy block for the filter rows [a_lo, a_lo + nrows):
 // acc[s][b] += sum_{py, px} dy[py][px] * x~[py + a_lo + s][px + b]   (tile-local)
 // `dyb` points at the staged dy of block row 0 (lane column), `xw` at the
 // staged x row (block row 0 + a_lo) at the lane's first column.
-template <int K, int AT, int DYP>
+template <int K, int AT, int DYP, int DR>
 __device__ __forceinline__ void dw_block(const float* __restrict__ dyb,
                                          const float* __restrict__ xw, int nrows,
                                          float (&acc)[AT][K]) {
   using G = Geo<K>;
-  float d[8][4];
+  float d[DR][4];
 #pragma unroll
-  for (int py = 0; py < 8; ++py) {
-    const float4 t = *reinterpret_cast<const float4*>(dyb + py * DYP);
+  for (int py = 0; py < DR; ++py) {
+    const float4 t = lds128_pinned(dyb + py * DYP);
     d[py][0] = t.x;
     d[py][1] = t.y;
     d[py][2] = t.z;
     d[py][3] = t.w;
   }
 #pragma unroll
-  for (int ir = 0; ir < 8 + AT - 1; ++ir) {
-    if (ir >= 8 + nrows - 1) break;
+  for (int ir = 0; ir < DR + AT - 1; ++ir) {
+    if (ir >= DR + nrows - 1) break;
     float buf[4 * G::NV];
     load_window_row<K>(xw + ir * G::SP, buf);
 #pragma unroll
     for (int s = 0; s < AT; ++s) {
       const int py = ir - s;
-      if (py >= 0 && py < 8 && s < nrows) {
+      if (py >= 0 && py < DR && s < nrows) {
 #pragma unroll
         for (int b = 0; b < K; ++b)
 #pragma unroll
@@ -214,6 +330,15 @@ __device__ __forceinline__ void dw_block(const float* __restrict__ dyb,
       }
     }
   }
+}
+
+// Rows per unrolled block in the backward roles: the input-gradient and the
+// filter-gradient warps run different unrolled bodies on the same SM, so for
+// K >= 7 both use 4-row blocks to keep the two bodies within the
+// instruction cache together.
+template <int K>
+constexpr int bwd_block_rows() {
+  return K <= 5 ? 8 : 4;
 }
 
 // ---------------------------------------------------------------- forward
@@ -239,14 +364,13 @@ __global__ void __launch_bounds__(kThreads) dw_fwd_kernel(const T* __restrict__ 
   const int64_t plane = t / tiles_y;
   const int c = (int)(plane % C);
 
-  const float* wc = w + (int64_t)c * K * K;
-  for (int k = threadIdx.x; k < K * K; k += kThreads) sm_w[k] = wc[flip ? K * K - 1 - k : k];
+  stage_filter<K>(sm_w, w + (int64_t)c * K * K, flip != 0, kThreads);
 
   const int ty0 = ty * TH, tx0 = tx * kTileW;
   const int64_t plane_off = plane * (int64_t)H * W;
   stage_tile<T, G::R, G::RP, G::SP>(sm_x, x + plane_off, H, W, ty0, tx0, TH + 2 * G::R,
                                     clamp != 0, vec != 0);
-  cta_barrier();
+  stage_wait();
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float acc[PY][4];
@@ -282,6 +406,7 @@ struct BwdShape {
   static constexpr int SM_FLOATS = SM_RED + NDW * AT * K;
   static_assert(NDW % GT == 0, "filter-row groups must divide the dw warps");
   static_assert(kBwdTileH % (WPG * 8) == 0, "dw warps own whole 8-row blocks");
+  static_assert(16 % bwd_block_rows<K>() == 0, "input-gradient warps own 16 rows");
 };
 
 __device__ __forceinline__ int group_lo(int g, int K, int GT) { return g * K / GT; }
@@ -309,10 +434,7 @@ __global__ void __launch_bounds__(kThreads, 2)
   const T* xp = x + plane_off;
   const T* dyp = dy + plane_off;
 
-  if (MODE == 0) {
-    const float* wc = w + (int64_t)c * K * K;
-    for (int k = threadIdx.x; k < K * K; k += kThreads) sm_w[k] = wc[K * K - 1 - k];
-  }
+  if (MODE == 0) stage_filter<K>(sm_w, w + (int64_t)c * K * K, true, kThreads);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -325,13 +447,14 @@ __global__ void __launch_bounds__(kThreads, 2)
                                         vec != 0);
       stage_tile<T, S::DY_HR, S::DY_HC, S::DY_P>(sm_dy, dyp, H, W, ty0, tx0, S::DY_ROWS, false,
                                                  vec != 0);
-      cta_barrier();
+      stage_wait();
+      constexpr int BR = bwd_block_rows<K>();
 #pragma unroll 1
-      for (int pass = 0; pass < 2; ++pass) {
-        const int r0 = warp * 16 + pass * 8;
-        float acc[8][4];
-        fwd_block<K, 8>(sm_dy + r0 * S::DY_P + 4 * lane, sm_w, acc);
-        store_block<T, 8>(dx + plane_off, H, W, ty0 + r0, tx0 + 4 * lane, vec != 0, acc);
+      for (int pass = 0; pass < 16 / BR; ++pass) {
+        const int r0 = warp * 16 + pass * BR;
+        float acc[BR][4];
+        fwd_block<K, BR>(sm_dy + r0 * S::DY_P + 4 * lane, sm_w, acc);
+        store_block<T, BR>(dx + plane_off, H, W, ty0 + r0, tx0 + 4 * lane, vec != 0, acc);
       }
     }
     cta_barrier();
@@ -355,11 +478,12 @@ __global__ void __launch_bounds__(kThreads, 2)
                                         vec != 0);
       stage_tile<T, S::DY_HR, S::DY_HC, S::DY_P>(sm_dy, dyp, H, W, ty0, tx0, S::DY_ROWS, false,
                                                  vec != 0);
-      cta_barrier();
+      stage_wait();
+      constexpr int BR = bwd_block_rows<K>();
 #pragma unroll 1
-      for (int r0 = part * S::DW_ROWS; r0 < (part + 1) * S::DW_ROWS; r0 += 8) {
-        dw_block<K, S::AT, S::DY_P>(sm_dy + (r0 + S::DY_HR) * S::DY_P + S::DY_HC + 4 * lane,
-                                    sm_x + (r0 + a_lo) * G::SP + 4 * lane, nrows, acc);
+      for (int r0 = part * S::DW_ROWS; r0 < (part + 1) * S::DW_ROWS; r0 += BR) {
+        dw_block<K, S::AT, S::DY_P, BR>(sm_dy + (r0 + S::DY_HR) * S::DY_P + S::DY_HC + 4 * lane,
+                                        sm_x + (r0 + a_lo) * G::SP + 4 * lane, nrows, acc);
       }
     }
     // warp reduction (fixed butterfly order), one row of sm_red per warp

@@ -103,10 +103,8 @@ __device__ __forceinline__ void rag_chunk(const RagParams& p, const RagChunk& ch
   // w may be NULL when neither the forward nor the input gradient is requested
   const float* wc = (do_fwd || do_dx) ? im.w + (int64_t)ch.channel * KK : nullptr;
   if (wc) {
-    for (int k = threadIdx.x; k < KK; k += kRagThreads) {
-      sm_w[k] = wc[k];
-      sm_wf[k] = wc[KK - 1 - k];
-    }
+    stage_filter<K>(sm_w, wc, false, kRagThreads);
+    stage_filter<K>(sm_wf, wc, true, kRagThreads);
   }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int role = warp >> 2, wl = warp & 3;
@@ -125,14 +123,15 @@ __device__ __forceinline__ void rag_chunk(const RagParams& p, const RagChunk& ch
       if (need_dy)
         stage_tile<T, G::R, G::RP, G::SP, kRagThreads>(sm_dy, dyp, H, W, ty0, tx0, S::ROWS,
                                                        false, vec);
-      cta_barrier();
+      stage_wait();
       if (active) {
+        constexpr int BR = bwd_block_rows<K>();
 #pragma unroll 1
-        for (int pass = 0; pass < 2; ++pass) {
-          const int r0 = wl * 16 + pass * 8;
-          float acc[8][4];
-          fwd_block<K, 8>(src + r0 * G::SP + 4 * lane, f, acc);
-          store_block<T, 8>(dst, H, W, ty0 + r0, tx0 + 4 * lane, vec, acc);
+        for (int pass = 0; pass < 16 / BR; ++pass) {
+          const int r0 = wl * 16 + pass * BR;
+          float acc[BR][4];
+          fwd_block<K, BR>(src + r0 * G::SP + 4 * lane, f, acc);
+          store_block<T, BR>(dst, H, W, ty0 + r0, tx0 + 4 * lane, vec, acc);
         }
       }
     }
@@ -157,12 +156,13 @@ __device__ __forceinline__ void rag_chunk(const RagParams& p, const RagChunk& ch
       if (need_dy)
         stage_tile<T, G::R, G::RP, G::SP, kRagThreads>(sm_dy, dyp, H, W, ty0, tx0, S::ROWS,
                                                        false, vec);
-      cta_barrier();
+      stage_wait();
       if (do_dw) {
+        constexpr int BR = bwd_block_rows<K>();
 #pragma unroll 1
-        for (int r0 = part * S::DW_ROWS; r0 < (part + 1) * S::DW_ROWS; r0 += 8)
-          dw_block<K, S::AT, G::SP>(sm_dy + (r0 + G::R) * G::SP + G::RP + 4 * lane,
-                                    sm_x + (r0 + a_lo) * G::SP + 4 * lane, nrows, acc);
+        for (int r0 = part * S::DW_ROWS; r0 < (part + 1) * S::DW_ROWS; r0 += BR)
+          dw_block<K, S::AT, G::SP, BR>(sm_dy + (r0 + G::R) * G::SP + G::RP + 4 * lane,
+                                        sm_x + (r0 + a_lo) * G::SP + 4 * lane, nrows, acc);
       }
     }
     cta_barrier();
