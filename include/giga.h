@@ -199,6 +199,11 @@ void giga_autotune_clear(void);
 
 /* ------------------------------------------------------------------------ */
 const char* giga_status_string(giga_status_t status);
+/* Synchronise `stream`, then read and clear the device error word that the
+ * pipelined tensor-core kernels set when a bounded wait on one of their
+ * barriers expires (they then stop issuing work and release their tensor
+ * memory instead of hanging).  Returns GIGA_ERR_TIMEOUT if it was set. */
+giga_status_t giga_check_device_error(void* stream);
 /* Description of the last error on the calling thread ("" if none). */
 const char* giga_last_error_detail(void);
 /* Kernel launches issued by this library on the calling thread since the last

@@ -207,3 +207,37 @@ class BatchedPlan:
             self.close()
         except Exception:
             pass
+
+
+# ------------------------------------------------------------ dense 3 x 3
+
+def dense_desc(x: torch.Tensor, K: int = 3, border="zero") -> _lib.giga_conv2d_desc_t:
+    N, H, W, C = x.shape
+    return _lib.desc(N, C, C, H, W, K, 1, _border(border), _dtype(x), _lib.GIGA_LAYOUT_NHWC)
+
+
+def dense_conv2d_fwd(x: torch.Tensor, w: torch.Tensor, out=None) -> torch.Tensor:
+    """Dense 3 x 3 filter, 64 -> 64 channels, BF16 NHWC, zero border (tcgen05).
+    x (N, H, W, 64), w (64, 3, 3, 64) = [C_out][K][K][C_in]."""
+    _require_cuda(x, w)
+    d = dense_desc(x, w.shape[1])
+    y = torch.empty_like(x) if out is None else out
+    _lib.check(_lib.giga_conv2d_fwd(d, _ptr(x), _ptr(w), _ptr(y), None, 0, _stream(x.device)),
+               "giga_conv2d_fwd (dense)")
+    return y
+
+
+def dense_conv2d_bwd_input(dy: torch.Tensor, w: torch.Tensor, out=None) -> torch.Tensor:
+    _require_cuda(dy, w)
+    d = dense_desc(dy, w.shape[1])
+    dx = torch.empty_like(dy) if out is None else out
+    ws = workspace(d, _lib.GIGA_OP_BWD_INPUT, dy.device)
+    _lib.check(_lib.giga_conv2d_bwd_input(d, _ptr(dy), _ptr(w), _ptr(dx), _ptr(ws), _nbytes(ws),
+                                          _stream(dy.device)), "giga_conv2d_bwd_input (dense)")
+    return dx
+
+
+def check_device_error(device=None) -> None:
+    """Raise if a pipelined tensor-core kernel reported an expired wait."""
+    dev = torch.device("cuda") if device is None else device
+    _lib.check(_lib.giga_check_device_error(_stream(dev)), "giga_check_device_error")

@@ -132,6 +132,47 @@ static giga_status_t check_ws(void* ws, size_t ws_bytes, size_t need) {
   return GIGA_OK;
 }
 
+// Dense path: 3 x 3, C_in = C_out = 64, BF16 NHWC, zero border; TMA needs
+// 16-byte aligned tensors.
+static giga_status_t check_dense(const giga_conv2d_desc_t* d) {
+  if (d->C_in != 64 || d->C_out != 64 || d->K != 3)
+    return fail(GIGA_ERR_UNSUPPORTED, "dense filtering supports 3 x 3 with C_in = C_out = 64");
+  if (d->dtype != GIGA_BF16 || d->layout != GIGA_LAYOUT_NHWC)
+    return fail(GIGA_ERR_UNSUPPORTED, "dense filtering takes BF16 NHWC tensors");
+  if (d->border != GIGA_BORDER_ZERO)
+    return fail(GIGA_ERR_UNSUPPORTED, "dense filtering supports the zero border");
+  if (d->N >= (1LL << 31) || d->H >= (1LL << 31))
+    return fail(GIGA_ERR_INVALID_ARG, "image too large");
+  return GIGA_OK;
+}
+
+static giga_status_t check_dense_ptr(const void* p, size_t numel, const char* name) {
+  if (numel == 0) return GIGA_OK;
+  if (!p) return fail(GIGA_ERR_INVALID_ARG, std::string(name) + " is NULL");
+  if (reinterpret_cast<uintptr_t>(p) % 16)
+    return fail(GIGA_ERR_MISALIGNED, std::string(name) + " must be 16-byte aligned (TMA)");
+  return GIGA_OK;
+}
+
+static giga_status_t dense_run(const giga_conv2d_desc_t* d, const void* in, const void* w,
+                               void* out, bool input_grad, void* ws, size_t ws_bytes,
+                               void* stream) {
+  giga_status_t s = check_dense(d);
+  if (s != GIGA_OK) return s;
+  const size_t n = (size_t)(d->N * d->H * d->W) * 64;
+  if ((s = check_dense_ptr(in, n, input_grad ? "dy" : "x")) ||
+      (s = check_dense_ptr(out, n, input_grad ? "dx" : "y")) ||
+      (s = check_dense_ptr(w, n ? 64 * 9 * 64 : 0, "w")))
+    return s;
+  if (overlap(in, out, n * 2)) return fail(GIGA_ERR_INVALID_ARG, "output aliases the input");
+  if (n == 0) return GIGA_OK;
+  if (input_grad && (s = check_ws(ws, ws_bytes, dense_workspace_bytes(true)))) return s;
+  cudaError_t e = dense_launch(in, w, out, d->N, d->H, d->W, input_grad, ws,
+                               static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "dense launch");
+  return GIGA_OK;
+}
+
 // --------------------------------------------------------------- dispatch
 
 template <typename F>
@@ -223,7 +264,10 @@ giga_status_t giga_conv2d_workspace_size(const giga_conv2d_desc_t* desc, int32_t
   if (s != GIGA_OK) return s;
   if (ops & ~(GIGA_OP_FWD | GIGA_OP_BWD_INPUT | GIGA_OP_BWD_FILTER))
     return fail(GIGA_ERR_INVALID_ARG, "unknown op bits");
-  if (!is_depthwise(desc)) return GIGA_OK;  // the dense path needs no workspace
+  if (!is_depthwise(desc)) {
+    if (ops & GIGA_OP_BWD_INPUT) *bytes = dense_workspace_bytes(true);
+    return GIGA_OK;
+  }
   if (ops & GIGA_OP_BWD_FILTER) *bytes = dw_filter_ws(desc);
   return GIGA_OK;
 }
@@ -233,9 +277,7 @@ giga_status_t giga_conv2d_fwd(const giga_conv2d_desc_t* desc, const void* x, con
   clear_error();
   giga_status_t s = check_desc(desc);
   if (s != GIGA_OK) return s;
-  (void)ws;
-  (void)ws_bytes;
-  if (!is_depthwise(desc)) return fail(GIGA_ERR_UNSUPPORTED, "dense filtering is not built");
+  if (!is_depthwise(desc)) return dense_run(desc, x, w, y, false, ws, ws_bytes, stream);
   const size_t es = elem_size(desc->dtype);
   const size_t n = (size_t)dw_numel(desc);
   if ((s = check_ptr(x, n, es, "x")) || (s = check_ptr(y, n, es, "y")) ||
@@ -257,9 +299,7 @@ giga_status_t giga_conv2d_bwd_input(const giga_conv2d_desc_t* desc, const void* 
   clear_error();
   giga_status_t s = check_desc(desc);
   if (s != GIGA_OK) return s;
-  (void)ws;
-  (void)ws_bytes;
-  if (!is_depthwise(desc)) return fail(GIGA_ERR_UNSUPPORTED, "dense filtering is not built");
+  if (!is_depthwise(desc)) return dense_run(desc, dy, w, dx, true, ws, ws_bytes, stream);
   const size_t es = elem_size(desc->dtype);
   const size_t n = (size_t)dw_numel(desc);
   if ((s = check_ptr(dy, n, es, "dy")) || (s = check_ptr(dx, n, es, "dx")) ||
@@ -395,6 +435,16 @@ const char* giga_status_string(giga_status_t status) {
 }
 
 const char* giga_last_error_detail(void) { return t_error.c_str(); }
+
+giga_status_t giga_check_device_error(void* stream) {
+  clear_error();
+  int code = 0;
+  cudaError_t e = dense_take_error(static_cast<cudaStream_t>(stream), &code);
+  if (e != cudaSuccess) return cuda_fail(e, "reading the device error word");
+  if (code != 0)
+    return fail(GIGA_ERR_TIMEOUT, "a tensor-core kernel gave up waiting on a pipeline barrier");
+  return GIGA_OK;
+}
 
 uint64_t giga_launch_count(void) { return t_launches; }
 

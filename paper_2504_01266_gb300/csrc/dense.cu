@@ -1,0 +1,481 @@
+// dense.cu -- the dense multi-channel 3 x 3 filter (C_in = C_out = 64, BF16
+// NHWC, zero border) as an implicit GEMM on the 5th-generation tensor cores.
+//
+//   y[n][i][j][o] = sum_{a,b,c} w[o][a][b][c] * x[n][i + a - 1][j + b - 1][c]
+//
+// is, for each tile of 128 consecutive output pixels of one image row, a
+// 128 x 64 x 576 GEMM: M = pixels, N = output channels, K = (tap, input
+// channel).  The 576-long K is walked as 9 taps x 64 channels; for tap (a, b)
+// the A operand is the 128 x 64 block of x shifted by (a - 1, b - 1), which a
+// TMA tensor load fetches directly from the NHWC tensor (out-of-range pixels
+// arrive as zeros: the zero border).  The GigaAPI paper only remarks that
+// convolution benefits from matrix multiplication (Section 3.1); this is that
+// contraction done on tcgen05.
+//
+// One persistent CTA per SM, 6 warps:
+//   warp 0    TMA producer: all 9 weight taps once (72 KB, resident), then the
+//             shifted activation blocks through a 6-stage ring (16 KB each);
+//   warp 1    allocates 128 TMEM columns (two 64-column FP32 accumulators) and
+//             one lane issues the tcgen05.mma chain (4 x K=16 per tap);
+//   warps 2-5 epilogue: tcgen05.ld of the accumulator (each warp reads its
+//             32-lane TMEM quadrant), convert to BF16, store the pixel rows.
+// Operands are K-major with the 128-byte swizzle the TMA writes.  Every
+// mbarrier wait is bounded: on expiry the CTA records an error code, stops
+// issuing work and frees its TMEM (the host reads the code back).
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+
+#include "common.cuh"
+
+namespace giga {
+
+constexpr int kDenseC = 64;          // input and output channels
+constexpr int kDenseTaps = 9;        // 3 x 3
+constexpr int kDenseTileM = 128;     // output pixels per tile
+constexpr int kDenseStages = 6;
+constexpr int kDenseThreads = 192;
+constexpr int kDenseABytes = kDenseTileM * kDenseC * 2;  // 16 KB
+constexpr int kDenseBBytes = kDenseC * kDenseC * 2;      // 8 KB per tap
+constexpr int kDenseTmemCols = 128;
+constexpr uint64_t kWaitLimitNs = 2000000000ull;  // give up a wait after 2 s
+
+constexpr size_t kDenseSmem = 1024 /* alignment slack */ + kDenseTaps * kDenseBBytes +
+                              kDenseStages * kDenseABytes + 256;
+
+// error codes written to *err (first one wins)
+enum { kDenseErrNone = 0, kDenseErrTimeout = 1 };
+
+// ------------------------------------------------------------- PTX helpers
+__device__ __forceinline__ uint32_t s_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(s_addr(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(s_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(s_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Wait for the phase with parity `parity` to complete; false after
+// kWaitLimitNs of wall time (the caller then records an error and stops).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t a = s_addr(bar);
+  const uint64_t t0 = global_ns();
+  for (;;) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (global_ns() - t0 > kWaitLimitNs) return false;
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int c0, int c1,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(s_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(s_addr(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int c0, int c1,
+                                            int c2, int c3, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(s_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(s_addr(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart (stride byte offset), descriptor version 1.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)1 << 16;             // leading byte offset (unused for this layout)
+  d |= (uint64_t)(1024 >> 4) << 32;   // stride byte offset
+  d |= (uint64_t)1 << 46;             // version
+  d |= (uint64_t)2 << 61;             // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor: D FP32, A and B BF16, both K-major, M = 128, N = 64.
+constexpr uint32_t kDenseIdesc = (1u << 4)     // D format F32
+                               | (1u << 7)     // A format BF16
+                               | (1u << 10)    // B format BF16
+                               | ((64u >> 3) << 17)    // N
+                               | ((128u >> 4) << 24);  // M
+
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                       uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          s_addr(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tc_wait_ld() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+struct DenseParams {
+  __nv_bfloat16* y;
+  int* err;
+  int N, H, W;
+  int tiles_w;
+  int64_t num_tiles;
+};
+
+__device__ __forceinline__ void dense_fail(int* err, volatile int* abort_flag) {
+  atomicCAS(err, kDenseErrNone, kDenseErrTimeout);
+  *abort_flag = 1;
+}
+
+__global__ void __launch_bounds__(kDenseThreads, 1)
+    dense_fwd_kernel(const __grid_constant__ CUtensorMap tmap_x,
+                     const __grid_constant__ CUtensorMap tmap_w, DenseParams p) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem =
+      reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* sB = smem;
+  uint8_t* sA = smem + kDenseTaps * kDenseBBytes;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sA + kDenseStages * kDenseABytes);
+  uint64_t* full = bars;
+  uint64_t* empty = bars + kDenseStages;
+  uint64_t* bfull = bars + 2 * kDenseStages;
+  uint64_t* tfull = bars + 2 * kDenseStages + 1;   // [2]
+  uint64_t* tempty = bars + 2 * kDenseStages + 3;  // [2]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kDenseStages + 5);
+  __shared__ volatile int s_abort;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    s_abort = 0;
+    for (int s = 0; s < kDenseStages; ++s) {
+      mbar_init(full + s, 1);
+      mbar_init(empty + s, 1);
+    }
+    mbar_init(bfull, 1);
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(tfull + a, 1);
+      mbar_init(tempty + a, 4 * 32);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     s_addr(tmem_slot)),
+                 "r"(kDenseTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------------------------------------------------- producer
+      mbar_expect_tx(bfull, kDenseTaps * kDenseBBytes);
+      for (int t = 0; t < kDenseTaps; ++t)
+        tma_load_2d(sB + t * kDenseBBytes, &tmap_w, t * kDenseC, 0, bfull);
+      int stage = 0;
+      uint32_t phase = 0;
+      for (int64_t tile = blockIdx.x; tile < p.num_tiles && !s_abort; tile += gridDim.x) {
+        const int jt = (int)(tile % p.tiles_w);
+        const int64_t r = tile / p.tiles_w;
+        const int i = (int)(r % p.H);
+        const int n = (int)(r / p.H);
+        const int j0 = jt * kDenseTileM;
+        for (int t = 0; t < kDenseTaps; ++t) {
+          if (!mbar_wait(empty + stage, phase ^ 1)) {
+            dense_fail(p.err, &s_abort);
+            break;
+          }
+          mbar_expect_tx(full + stage, kDenseABytes);
+          tma_load_4d(sA + stage * kDenseABytes, &tmap_x, 0, j0 + t % 3 - 1, i + t / 3 - 1, n,
+                      full + stage);
+          if (++stage == kDenseStages) {
+            stage = 0;
+            phase ^= 1;
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ------------------------------------------------------- MMA issuer
+      bool ok = mbar_wait(bfull, 0);
+      if (!ok) dense_fail(p.err, &s_abort);
+      int stage = 0;
+      uint32_t phase = 0;
+      int acc = 0;
+      uint32_t acc_phase = 0;
+      const uint32_t b_base = s_addr(sB);
+      for (int64_t tile = blockIdx.x; ok && tile < p.num_tiles && !s_abort; tile += gridDim.x) {
+        if (!mbar_wait(tempty + acc, acc_phase ^ 1)) {
+          dense_fail(p.err, &s_abort);
+          break;
+        }
+        tc_fence_after();
+        const uint32_t d_tmem = tmem_base + (uint32_t)(acc * 64);
+        for (int t = 0; t < kDenseTaps; ++t) {
+          if (!mbar_wait(full + stage, phase)) {
+            dense_fail(p.err, &s_abort);
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a_base = s_addr(sA + stage * kDenseABytes);
+#pragma unroll
+          for (int k = 0; k < kDenseC / 16; ++k) {
+            tc_mma(d_tmem, sw128_desc(a_base + 32 * k),
+                   sw128_desc(b_base + t * kDenseBBytes + 32 * k), kDenseIdesc,
+                   (t > 0 || k > 0) ? 1u : 0u);
+          }
+          tc_commit(empty + stage);  // frees the stage once these MMAs finish
+          if (++stage == kDenseStages) {
+            stage = 0;
+            phase ^= 1;
+          }
+        }
+        if (!ok) break;
+        tc_commit(tfull + acc);  // accumulator ready for the epilogue
+        if (++acc == 2) {
+          acc = 0;
+          acc_phase ^= 1;
+        }
+      }
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue
+    const int quad = warp & 3;  // TMEM lane quadrant this warp may access
+    const int row = quad * 32 + lane;
+    int acc = 0;
+    uint32_t acc_phase = 0;
+    for (int64_t tile = blockIdx.x; tile < p.num_tiles && !s_abort; tile += gridDim.x) {
+      if (!mbar_wait(tfull + acc, acc_phase)) {
+        dense_fail(p.err, &s_abort);
+        break;
+      }
+      tc_fence_after();
+      const uint32_t taddr = tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(acc * 64);
+      float v[64];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        float part[16];
+        tc_ld16(taddr + 16 * c, part);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) v[16 * c + q] = part[q];
+      }
+      tc_wait_ld();
+      tc_fence_before();
+      mbar_arrive(tempty + acc);
+      const int jt = (int)(tile % p.tiles_w);
+      const int64_t r = tile / p.tiles_w;  // n * H + i
+      const int j = jt * kDenseTileM + row;
+      if (j < p.W) {
+        uint4* dst = reinterpret_cast<uint4*>(p.y + ((r * p.W + j) * kDenseC));
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          uint4 u;
+          __nv_bfloat162 h0 = __floats2bfloat162_rn(v[8 * q + 0], v[8 * q + 1]);
+          __nv_bfloat162 h1 = __floats2bfloat162_rn(v[8 * q + 2], v[8 * q + 3]);
+          __nv_bfloat162 h2 = __floats2bfloat162_rn(v[8 * q + 4], v[8 * q + 5]);
+          __nv_bfloat162 h3 = __floats2bfloat162_rn(v[8 * q + 6], v[8 * q + 7]);
+          u.x = *reinterpret_cast<uint32_t*>(&h0);
+          u.y = *reinterpret_cast<uint32_t*>(&h1);
+          u.z = *reinterpret_cast<uint32_t*>(&h2);
+          u.w = *reinterpret_cast<uint32_t*>(&h3);
+          dst[q] = u;
+        }
+      }
+      if (++acc == 2) {
+        acc = 0;
+        acc_phase ^= 1;
+      }
+    }
+  }
+
+  // Drain: the MMA issuer's last commits must land before TMEM is freed.
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    __syncwarp();
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                 "r"(kDenseTmemCols)
+                 : "memory");
+  }
+}
+
+// dgrad filter: wt[c][a][b][o] = w[o][2 - a][2 - b][c] (rotate the taps,
+// swap the channel roles), so the input gradient is the same forward kernel
+// run on dy.
+__global__ void dense_flip_weights_kernel(const __nv_bfloat16* __restrict__ w,
+                                          __nv_bfloat16* __restrict__ wt) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= kDenseC * kDenseTaps * kDenseC) return;
+  const int o = idx % kDenseC;
+  const int tap = (idx / kDenseC) % kDenseTaps;
+  const int c = idx / (kDenseC * kDenseTaps);
+  const int a = tap / 3, b = tap % 3;
+  wt[idx] = w[((o * 3 + (2 - a)) * 3 + (2 - b)) * kDenseC + c];
+}
+
+// ------------------------------------------------------------------ host
+using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                              const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                              const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                              CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeFn encode_fn() {
+  static EncodeFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeFn>(p);
+  });
+  return fn;
+}
+
+static __device__ int g_dense_err;
+
+size_t dense_workspace_bytes(bool input_grad) {
+  return input_grad ? (size_t)(kDenseC * kDenseTaps * kDenseC * 2 + 255) / 256 * 256 : 0;
+}
+
+// x [N][H][W][64] BF16, w [64][3][3][64] BF16 -> y [N][H][W][64] BF16.
+// input_grad: x is dy, w is flipped into `ws` first, y is dx.
+cudaError_t dense_launch(const void* x, const void* w, void* y, int64_t N, int64_t H, int64_t W,
+                         bool input_grad, void* ws, cudaStream_t st) {
+  EncodeFn enc = encode_fn();
+  if (!enc) return cudaErrorNotSupported;
+  const void* wk = w;
+  if (input_grad) {
+    const int n = kDenseC * kDenseTaps * kDenseC;
+    dense_flip_weights_kernel<<<(n + 255) / 256, 256, 0, st>>>(
+        static_cast<const __nv_bfloat16*>(w), static_cast<__nv_bfloat16*>(ws));
+    note_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    wk = ws;
+  }
+  CUtensorMap tx, tw;
+  {
+    cuuint64_t dims[4] = {(cuuint64_t)kDenseC, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)N};
+    cuuint64_t strides[3] = {(cuuint64_t)kDenseC * 2, (cuuint64_t)W * kDenseC * 2,
+                             (cuuint64_t)H * W * kDenseC * 2};
+    cuuint32_t box[4] = {(cuuint32_t)kDenseC, (cuuint32_t)kDenseTileM, 1, 1};
+    cuuint32_t estr[4] = {1, 1, 1, 1};
+    if (enc(&tx, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(x), dims, strides, box,
+            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return cudaErrorInvalidValue;
+  }
+  {
+    cuuint64_t dims[2] = {(cuuint64_t)kDenseTaps * kDenseC, (cuuint64_t)kDenseC};
+    cuuint64_t strides[1] = {(cuuint64_t)kDenseTaps * kDenseC * 2};
+    cuuint32_t box[2] = {(cuuint32_t)kDenseC, (cuuint32_t)kDenseC};
+    cuuint32_t estr[2] = {1, 1};
+    if (enc(&tw, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(wk), dims, strides, box,
+            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return cudaErrorInvalidValue;
+  }
+  int* err = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(reinterpret_cast<void**>(&err), g_dense_err);
+  if (e != cudaSuccess) return e;
+  e = set_smem_once<dense_fwd_kernel>(kDenseSmem);
+  if (e != cudaSuccess) return e;
+  DenseParams prm;
+  prm.y = static_cast<__nv_bfloat16*>(y);
+  prm.err = err;
+  prm.N = (int)N;
+  prm.H = (int)H;
+  prm.W = (int)W;
+  prm.tiles_w = (int)((W + kDenseTileM - 1) / kDenseTileM);
+  prm.num_tiles = N * H * prm.tiles_w;
+  int sms = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = (int)std::min<int64_t>(prm.num_tiles, (int64_t)(sms > 0 ? sms : 148));
+  dense_fwd_kernel<<<grid, kDenseThreads, kDenseSmem, st>>>(tx, tw, prm);
+  note_launch();
+  return cudaGetLastError();
+}
+
+// Reads and clears the device error word of the dense kernels (synchronises
+// the stream first).  Returns 0 or a kDenseErr* code.
+cudaError_t dense_take_error(cudaStream_t st, int* code) {
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return e;
+  int* err = nullptr;
+  e = cudaGetSymbolAddress(reinterpret_cast<void**>(&err), g_dense_err);
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpy(code, err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return e;
+  const int zero = 0;
+  return cudaMemcpy(err, &zero, sizeof(int), cudaMemcpyHostToDevice);
+}
+
+}  // namespace giga

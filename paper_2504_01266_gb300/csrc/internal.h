@@ -30,4 +30,10 @@ giga_status_t run_dw_op(int op, const DwArgs& a, const DwConfig& cfg, cudaStream
 // Benchmark all candidates of `op` on these buffers and store the fastest.
 giga_status_t tune_dw_op(int op, const DwArgs& a, cudaStream_t st);
 
+// Dense 3 x 3, 64 -> 64 channel path (dense.cu).
+size_t dense_workspace_bytes(bool input_grad);
+cudaError_t dense_launch(const void* x, const void* w, void* y, int64_t N, int64_t H, int64_t W,
+                         bool input_grad, void* ws, cudaStream_t st);
+cudaError_t dense_take_error(cudaStream_t st, int* code);
+
 }  // namespace giga
