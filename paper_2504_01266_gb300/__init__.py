@@ -241,3 +241,14 @@ def check_device_error(device=None) -> None:
     """Raise if a pipelined tensor-core kernel reported an expired wait."""
     dev = torch.device("cuda") if device is None else device
     _lib.check(_lib.giga_check_device_error(_stream(dev)), "giga_check_device_error")
+
+
+def dense_conv2d_bwd_filter(x: torch.Tensor, dy: torch.Tensor, out=None) -> torch.Tensor:
+    """Filter gradient of the dense 3 x 3 filter: FP32 (64, 3, 3, 64)."""
+    _require_cuda(x, dy)
+    d = dense_desc(x, 3)
+    dw = torch.empty((64, 3, 3, 64), dtype=torch.float32, device=x.device) if out is None else out
+    ws = workspace(d, _lib.GIGA_OP_BWD_FILTER, x.device)
+    _lib.check(_lib.giga_conv2d_bwd_filter(d, _ptr(x), _ptr(dy), _ptr(dw), _ptr(ws), _nbytes(ws),
+                                           _stream(x.device)), "giga_conv2d_bwd_filter (dense)")
+    return dw

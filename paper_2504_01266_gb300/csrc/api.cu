@@ -2,6 +2,7 @@
 // workspace sizing, dispatch to the depthwise kernels, status reporting.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cstdint>
 #include <cstring>
@@ -266,6 +267,7 @@ giga_status_t giga_conv2d_workspace_size(const giga_conv2d_desc_t* desc, int32_t
     return fail(GIGA_ERR_INVALID_ARG, "unknown op bits");
   if (!is_depthwise(desc)) {
     if (ops & GIGA_OP_BWD_INPUT) *bytes = dense_workspace_bytes(true);
+    if (ops & GIGA_OP_BWD_FILTER) *bytes = std::max(*bytes, dense_filter_workspace_bytes());
     return GIGA_OK;
   }
   if (ops & GIGA_OP_BWD_FILTER) *bytes = dw_filter_ws(desc);
@@ -320,7 +322,22 @@ static giga_status_t bwd_common(const giga_conv2d_desc_t* desc, const void* x, c
                                 void* stream, bool fused) {
   giga_status_t s = check_desc(desc);
   if (s != GIGA_OK) return s;
-  if (!is_depthwise(desc)) return fail(GIGA_ERR_UNSUPPORTED, "dense filtering is not built");
+  if (!is_depthwise(desc)) {
+    if (fused) return fail(GIGA_ERR_UNSUPPORTED, "the fused backward pass is depthwise only");
+    if ((s = check_dense(desc))) return s;
+    const size_t n = (size_t)(desc->N * desc->H * desc->W) * 64;
+    if ((s = check_dense_ptr(x, n, "x")) || (s = check_dense_ptr(dy, n, "dy")) ||
+        (s = check_ptr(dw, 64 * 9 * 64, 4, "dw")))
+      return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (n == 0) {
+      cudaError_t e = cudaMemsetAsync(dw, 0, sizeof(float) * 64 * 9 * 64, st);
+      return e == cudaSuccess ? GIGA_OK : cuda_fail(e, "zeroing dw");
+    }
+    if ((s = check_ws(ws, ws_bytes, dense_filter_workspace_bytes()))) return s;
+    cudaError_t e = dense_wgrad_launch(x, dy, dw, desc->N, desc->H, desc->W, ws, st);
+    return e == cudaSuccess ? GIGA_OK : cuda_fail(e, "dense filter-gradient launch");
+  }
   if (desc->K > kMaxKFilter)
     return fail(GIGA_ERR_UNSUPPORTED, "the filter gradient supports K <= 15");
   const size_t es = elem_size(desc->dtype);

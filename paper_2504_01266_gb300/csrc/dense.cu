@@ -130,12 +130,28 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
   return d;
 }
 
+// The same 128-byte-swizzled layout read as MN-major (the contiguous 128-byte
+// rows hold 64 elements of M or N; consecutive rows step along K): 8-row K
+// groups 1024 bytes apart, successive 64-element M/N blocks `lbo` bytes apart.
+__device__ __forceinline__ uint64_t sw128_desc_mn(uint32_t saddr, uint32_t lbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
 // Instruction descriptor: D FP32, A and B BF16, both K-major, M = 128, N = 64.
 constexpr uint32_t kDenseIdesc = (1u << 4)     // D format F32
                                | (1u << 7)     // A format BF16
                                | (1u << 10)    // B format BF16
                                | ((64u >> 3) << 17)    // N
                                | ((128u >> 4) << 24);  // M
+
+// Same shape with both operands MN-major (filter gradient).
+constexpr uint32_t kDenseIdescMN = kDenseIdesc | (1u << 15) | (1u << 16);
 
 __device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
                                        uint32_t accumulate) {
@@ -364,6 +380,190 @@ __global__ void __launch_bounds__(kDenseThreads, 1)
   }
 }
 
+// ------------------------------------------------------- filter gradient
+//   dw[o][a][b][c] = sum_{n,i,j} dy[n][i][j][o] * x[n][i + a - 1][j + b - 1][c]
+// For a chunk of 64 pixels of one image row, a TMA load of the shifted x
+// block of tap t is a 64-pixel x 64-channel tile whose 128-byte rows are
+// pixels: read as MN-major it is the K x M operand (K = pixels, M = input
+// channels).  Two taps' tiles placed 8 KB apart form one M = 128 operand
+// (rows 0-63: tap 2q, rows 64-127: tap 2q + 1); the dy tile is the K x N
+// operand (N = output channels).  D[(tap, c)][o] accumulates in TMEM over all
+// pixel chunks of the CTA: 5 tap pairs x 64 columns (the 10th tap slot is a
+// zero tile).  Each CTA then writes its 5 x 128 x 64 FP32 partial sums and a
+// second kernel adds the CTAs' partials in FP64 in CTA order.
+constexpr int kWgTileP = 64;                    // pixels per chunk
+constexpr int kWgTileBytes = kWgTileP * kDenseC * 2;  // 8 KB
+constexpr int kWgSlots = 11;                    // 9 taps + zero tile + dy
+constexpr int kWgStageBytes = kWgSlots * kWgTileBytes;
+constexpr int kWgStages = 2;
+constexpr int kWgPairs = 5;
+constexpr int kWgTmemCols = 512;
+constexpr size_t kWgSmem = 1024 + kWgStages * kWgStageBytes + 256;
+constexpr int64_t kWgPartialFloats = (int64_t)kWgPairs * 128 * kDenseC;
+
+struct WgParams {
+  float* partials;  // [grid][5][128][64]
+  int* err;
+  int N, H, W;
+  int tiles_w;
+  int64_t num_tiles;
+};
+
+__global__ void __launch_bounds__(kDenseThreads, 1)
+    dense_wgrad_kernel(const __grid_constant__ CUtensorMap tmap_x,
+                       const __grid_constant__ CUtensorMap tmap_dy, WgParams p) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem =
+      reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kWgStages * kWgStageBytes);
+  uint64_t* full = bars;
+  uint64_t* empty = bars + kWgStages;
+  uint64_t* done = bars + 2 * kWgStages;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kWgStages + 1);
+  __shared__ volatile int s_abort;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  // zero tile (slot 9) of every stage: written once, never loaded into
+  for (int st = 0; st < kWgStages; ++st) {
+    uint4* z = reinterpret_cast<uint4*>(smem + st * kWgStageBytes + 9 * kWgTileBytes);
+    for (int k = threadIdx.x; k < kWgTileBytes / 16; k += kDenseThreads) z[k] = make_uint4(0, 0, 0, 0);
+  }
+  if (threadIdx.x == 0) {
+    s_abort = 0;
+    for (int st = 0; st < kWgStages; ++st) {
+      mbar_init(full + st, 1);
+      mbar_init(empty + st, 1);
+    }
+    mbar_init(done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  // make the generic-proxy zero tiles visible to the tensor cores
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     s_addr(tmem_slot)),
+                 "r"(kWgTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      for (int64_t tile = blockIdx.x; tile < p.num_tiles && !s_abort; tile += gridDim.x) {
+        const int jt = (int)(tile % p.tiles_w);
+        const int64_t r = tile / p.tiles_w;
+        const int i = (int)(r % p.H), n = (int)(r / p.H);
+        const int j0 = jt * kWgTileP;
+        if (!mbar_wait(empty + stage, phase ^ 1)) {
+          dense_fail(p.err, &s_abort);
+          break;
+        }
+        uint8_t* base = smem + stage * kWgStageBytes;
+        mbar_expect_tx(full + stage, 10 * kWgTileBytes);
+        for (int t = 0; t < kDenseTaps; ++t)
+          tma_load_4d(base + t * kWgTileBytes, &tmap_x, 0, j0 + t % 3 - 1, i + t / 3 - 1, n,
+                      full + stage);
+        tma_load_4d(base + 10 * kWgTileBytes, &tmap_dy, 0, j0, i, n, full + stage);
+        if (++stage == kWgStages) {
+          stage = 0;
+          phase ^= 1;
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      bool first = true, ok = true;
+      for (int64_t tile = blockIdx.x; tile < p.num_tiles && !s_abort; tile += gridDim.x) {
+        if (!mbar_wait(full + stage, phase)) {
+          dense_fail(p.err, &s_abort);
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t base = s_addr(smem + stage * kWgStageBytes);
+        const uint32_t dy_base = base + 10 * kWgTileBytes;
+#pragma unroll
+        for (int q = 0; q < kWgPairs; ++q) {
+#pragma unroll
+          for (int k = 0; k < kWgTileP / 16; ++k) {
+            tc_mma(tmem_base + (uint32_t)(q * 64),
+                   sw128_desc_mn(base + 2 * q * kWgTileBytes + k * 2048, kWgTileBytes),
+                   sw128_desc_mn(dy_base + k * 2048, kWgTileBytes), kDenseIdescMN,
+                   (first && k == 0) ? 0u : 1u);
+          }
+        }
+        first = false;
+        tc_commit(empty + stage);
+        if (++stage == kWgStages) {
+          stage = 0;
+          phase ^= 1;
+        }
+      }
+      if (ok) tc_commit(done);  // fires once every MMA above has completed
+      else mbar_arrive(done);
+    }
+  } else {
+    // epilogue: TMEM -> FP32 partials of this CTA
+    const int quad = warp & 3;
+    const int row = quad * 32 + lane;
+    const bool any = (int64_t)blockIdx.x < p.num_tiles;
+    if (any && mbar_wait(done, 0) && !s_abort) {
+      tc_fence_after();
+      float* out = p.partials + (int64_t)blockIdx.x * kWgPartialFloats;
+      for (int q = 0; q < kWgPairs; ++q) {
+        float v[64];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          float part[16];
+          tc_ld16(tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(q * 64 + 16 * c), part);
+#pragma unroll
+          for (int z = 0; z < 16; ++z) v[16 * c + z] = part[z];
+        }
+        tc_wait_ld();
+        float4* dst = reinterpret_cast<float4*>(out + ((int64_t)q * 128 + row) * kDenseC);
+#pragma unroll
+        for (int z = 0; z < 16; ++z)
+          dst[z] = make_float4(v[4 * z], v[4 * z + 1], v[4 * z + 2], v[4 * z + 3]);
+      }
+    } else if (any) {
+      dense_fail(p.err, &s_abort);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    __syncwarp();
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                 "r"(kWgTmemCols)
+                 : "memory");
+  }
+}
+
+// dw[o][a][b][c] = sum over CTAs (in order, FP64) of partial[cta][q][row][o]
+// with tap = 2q + row / 64, c = row % 64.
+__global__ void dense_wgrad_finalize_kernel(const float* __restrict__ partials, int ctas,
+                                            float* __restrict__ dw) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= kDenseC * kDenseTaps * kDenseC) return;
+  const int c = idx % kDenseC;
+  const int tap = (idx / kDenseC) % kDenseTaps;
+  const int o = idx / (kDenseC * kDenseTaps);
+  const int q = tap / 2, row = (tap % 2) * 64 + c;
+  double s = 0.0;
+  for (int b = 0; b < ctas; ++b)
+    s += (double)partials[(int64_t)b * kWgPartialFloats + ((int64_t)q * 128 + row) * kDenseC + o];
+  dw[idx] = (float)s;
+}
+
 // dgrad filter: wt[c][a][b][o] = w[o][2 - a][2 - b][c] (rotate the taps,
 // swap the channel roles), so the input gradient is the same forward kernel
 // run on dy.
@@ -400,8 +600,69 @@ static EncodeFn encode_fn() {
 
 static __device__ int g_dense_err;
 
+// The filter-gradient grid never exceeds this many CTAs (it is also capped by
+// the SM count), so its workspace size does not depend on the device.
+constexpr int kWgMaxCtas = 256;
+
 size_t dense_workspace_bytes(bool input_grad) {
   return input_grad ? (size_t)(kDenseC * kDenseTaps * kDenseC * 2 + 255) / 256 * 256 : 0;
+}
+
+size_t dense_filter_workspace_bytes() {
+  return (size_t)kWgMaxCtas * kWgPartialFloats * sizeof(float);
+}
+
+static bool make_nhwc_map(EncodeFn enc, CUtensorMap* m, const void* base, int64_t N, int64_t H,
+                          int64_t W, int box_px) {
+  cuuint64_t dims[4] = {(cuuint64_t)kDenseC, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)N};
+  cuuint64_t strides[3] = {(cuuint64_t)kDenseC * 2, (cuuint64_t)W * kDenseC * 2,
+                           (cuuint64_t)H * W * kDenseC * 2};
+  cuuint32_t box[4] = {(cuuint32_t)kDenseC, (cuuint32_t)box_px, 1, 1};
+  cuuint32_t estr[4] = {1, 1, 1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(base), dims, strides, box,
+             estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+static int device_sms() {
+  int sms = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms > 0 ? sms : 148;
+}
+
+// dw [64][3][3][64] FP32 = filter gradient of x, dy (NHWC BF16); ws holds the
+// per-CTA partial sums (dense_filter_workspace_bytes()).
+cudaError_t dense_wgrad_launch(const void* x, const void* dy, float* dw, int64_t N, int64_t H,
+                               int64_t W, void* ws, cudaStream_t st) {
+  EncodeFn enc = encode_fn();
+  if (!enc) return cudaErrorNotSupported;
+  CUtensorMap tx, tdy;
+  if (!make_nhwc_map(enc, &tx, x, N, H, W, kWgTileP) ||
+      !make_nhwc_map(enc, &tdy, dy, N, H, W, kWgTileP))
+    return cudaErrorInvalidValue;
+  int* err = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(reinterpret_cast<void**>(&err), g_dense_err);
+  if (e != cudaSuccess) return e;
+  e = set_smem_once<dense_wgrad_kernel>(kWgSmem);
+  if (e != cudaSuccess) return e;
+  WgParams prm;
+  prm.partials = static_cast<float*>(ws);
+  prm.err = err;
+  prm.N = (int)N;
+  prm.H = (int)H;
+  prm.W = (int)W;
+  prm.tiles_w = (int)((W + kWgTileP - 1) / kWgTileP);
+  prm.num_tiles = N * H * prm.tiles_w;
+  const int grid = (int)std::min<int64_t>(std::min<int64_t>(prm.num_tiles, device_sms()),
+                                          kWgMaxCtas);
+  dense_wgrad_kernel<<<grid, kDenseThreads, kWgSmem, st>>>(tx, tdy, prm);
+  note_launch();
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const int n = kDenseC * kDenseTaps * kDenseC;
+  dense_wgrad_finalize_kernel<<<(n + 255) / 256, 256, 0, st>>>(prm.partials, grid, dw);
+  note_launch();
+  return cudaGetLastError();
 }
 
 // x [N][H][W][64] BF16, w [64][3][3][64] BF16 -> y [N][H][W][64] BF16.

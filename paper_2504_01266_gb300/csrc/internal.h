@@ -35,5 +35,8 @@ size_t dense_workspace_bytes(bool input_grad);
 cudaError_t dense_launch(const void* x, const void* w, void* y, int64_t N, int64_t H, int64_t W,
                          bool input_grad, void* ws, cudaStream_t st);
 cudaError_t dense_take_error(cudaStream_t st, int* code);
+size_t dense_filter_workspace_bytes();
+cudaError_t dense_wgrad_launch(const void* x, const void* dy, float* dw, int64_t N, int64_t H,
+                               int64_t W, void* ws, cudaStream_t st);
 
 }  // namespace giga

@@ -8,7 +8,7 @@ import torch
 
 import oracle
 import workloads
-from helpers import BF16_KERNEL_TOL, normwise, to_np
+from helpers import BF16_KERNEL_TOL, FP32_TOL, gamma, normwise, to_np
 
 
 @pytest.fixture(scope="module")
@@ -39,6 +39,26 @@ def test_dense_fwd_and_input_grad(giga, shape):
     xr, wr, dyr = x.double().numpy(), w.double().numpy(), dy.double().numpy()
     assert normwise(to_np(y), oracle.dense_fwd(xr, wr, oracle.ZERO)) <= BF16_KERNEL_TOL
     assert normwise(to_np(dx), oracle.dense_bwd_input(dyr, wr, oracle.ZERO)) <= BF16_KERNEL_TOL
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("shape", [(1, 1, 1), (2, 5, 200), (1, 3, 300), (3, 17, 64)])
+def test_dense_filter_grad(giga, shape):
+    """dw[o][a][b][c] = sum_{n,i,j} dy[n,i,j,o] x~[n,i+a-1,j+b-1,c] on the tensor
+    cores (FP32 accumulation), FP64 across CTAs.  Bound: the FP32 accumulation
+    bound 2 * gamma(n) * sum|terms| with n = N*H*W products per tap."""
+    N, H, W = shape
+    x, w, dy = make(N, H, W, 7 + sum(shape))
+    dw = giga.dense_conv2d_bwd_filter(x.cuda(), dy.cuda(),
+                                      out=torch.full((64, 3, 3, 64), float("nan"), device="cuda"))
+    giga.check_device_error()
+    xr, dyr = x.double().numpy(), dy.double().numpy()
+    ref = oracle.dense_bwd_filter(xr, dyr, 3, oracle.ZERO)
+    mag = oracle.dense_bwd_filter(np.abs(xr), np.abs(dyr), 3, oracle.ZERO)
+    got = to_np(dw)
+    assert not np.isnan(got).any()
+    assert (np.abs(got - ref) <= 2 * gamma(N * H * W) * mag + 1e-30).all()
+    assert normwise(got, ref) <= FP32_TOL
 
 
 @pytest.mark.gpu
