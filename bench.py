@@ -199,6 +199,187 @@ def run_reference(args):
     return 0
 
 
+# -------------------------------------------------------- comparisons
+
+def _events(stream, fn, iters):
+    """Median per-iteration milliseconds of fn() over `iters` runs, CUDA events
+    on the launching stream, after one warm-up."""
+    import torch
+    fn()
+    times = []
+    for _ in range(iters):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        b.synchronize()
+        times.append(a.elapsed_time(b))
+    return statistics.median(times)
+
+
+def _normwise(got, ref):
+    import numpy as np
+    got, ref = np.asarray(got, np.float64), np.asarray(ref, np.float64)
+    return float(np.abs(got - ref).max() / max(np.abs(ref).max(), 1e-300))
+
+
+def compare_bf16(dev, iters):
+    """BF16 storage (FP32 accumulation) vs FP32 storage on 32 x 3 x 2048 x 2048,
+    9 x 9 filters, zero border: fwd + fused bwd, with the normwise error of
+    sampled outputs against the FP64 oracle (i) on the BF16-rounded inputs and
+    (ii) on the FP32 originals."""
+    import torch
+    import oracle
+    import workloads
+    from paper_2504_01266_gb300 import _lib as L
+    Nb, Cb, Hb, Wb, Kb = 32, 3, 2048, 2048, 9
+    g = torch.Generator(device=dev)
+    g.manual_seed(2504 + 4)
+    x32 = torch.rand((Nb, Cb, Hb, Wb), generator=g, device=dev)
+    dy32 = torch.randn((Nb, Cb, Hb, Wb), generator=g, device=dev)
+    w = (torch.randn((Cb, Kb, Kb), generator=torch.Generator().manual_seed(2508)) * 0.1).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    sp = stream.cuda_stream
+    out = {}
+    res = {}
+    for name, dt in (("fp32", torch.float32), ("bf16", torch.bfloat16)):
+        x, dy = x32.to(dt), dy32.to(dt)
+        y, dx = torch.empty_like(x), torch.empty_like(x)
+        dw = torch.empty((Cb, Kb, Kb), device=dev)
+        d = L.desc(Nb, Cb, Cb, Hb, Wb, Kb, Cb, 0, L.GIGA_F32 if dt == torch.float32 else L.GIGA_BF16,
+                   L.GIGA_LAYOUT_NCHW)
+        wsb = L.giga_conv2d_workspace_size(d, 6)
+        ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+        L.check(L.giga_autotune_conv2d(d, 7, x.data_ptr(), w.data_ptr(), y.data_ptr(),
+                                       dy.data_ptr(), dx.data_ptr(), dw.data_ptr(), ws.data_ptr(),
+                                       wsb, sp), "autotune")
+
+        def run():
+            L.check(L.giga_conv2d_fwd(d, x.data_ptr(), w.data_ptr(), y.data_ptr(), None, 0, sp), "fwd")
+            L.check(L.giga_conv2d_bwd(d, x.data_ptr(), dy.data_ptr(), w.data_ptr(), dx.data_ptr(),
+                                      dw.data_ptr(), ws.data_ptr(), wsb, sp), "bwd")
+        ms = _events(stream, run, iters)
+        px = Nb * Cb * Hb * Wb
+        out[name] = {"ms": ms, "value": 3 * px * Kb * Kb / (ms * 1e-3) / 1e9,
+                     "bytes_per_px": (20 if dt == torch.float32 else 10)}
+        res[name] = (x, dy, y, dx, dw)
+        del ws
+    # sampled errors against the FP64 oracle (one image's planes, 1500 points)
+    idx = workloads.sample_indices(Cb * Hb * Wb, 1500, salt=9)
+    xb0 = res["bf16"][0][0:1].float().cpu().numpy()
+    dyb0 = res["bf16"][1][0:1].float().cpu().numpy()
+    x0, dy0, wn = x32[0:1].cpu().numpy(), dy32[0:1].cpu().numpy(), w.cpu().numpy()
+    errs = {}
+    for name in ("fp32", "bf16"):
+        x, dy, y, dx, dw = res[name]
+        gy = y[0:1].reshape(-1)[idx.to(dev)].double().cpu().numpy()
+        gdx = dx[0:1].reshape(-1)[idx.to(dev)].double().cpu().numpy()
+        xin, dyin = (x0, dy0) if name == "fp32" else (xb0, dyb0)
+        e = {"y": _normwise(gy, oracle.dw_fwd_points(xin, wn, 0, idx.numpy())),
+             "dx": _normwise(gdx, oracle.dw_bwd_input_points(dyin, wn, 0, idx.numpy()))}
+        if name == "bf16":
+            e["y_vs_fp32_inputs"] = _normwise(gy, oracle.dw_fwd_points(x0, wn, 0, idx.numpy()))
+            e["dx_vs_fp32_inputs"] = _normwise(gdx, oracle.dw_bwd_input_points(dy0, wn, 0,
+                                                                                idx.numpy()))
+        errs[name] = e
+    out["fp32"]["err_normwise_sampled"] = errs["fp32"]
+    out["bf16"]["err_normwise_sampled"] = errs["bf16"]
+    out["bf16_over_fp32"] = out["bf16"]["value"] / out["fp32"]["value"]
+    out["workload"] = "32x3x2048x2048, K=9 normal(0,0.1), zero border, fwd+bwd"
+    return out
+
+
+def compare_ragged(dev, iters):
+    """256 ragged 3-channel images (H, W uniform in [64, 4096], K in {3,5,9,11}),
+    zero border, fwd + both gradients: one persistent launch replayed from a CUDA
+    graph vs a loop of per-image FP32 calls on the same GPU."""
+    import torch
+    import workloads
+    import paper_2504_01266_gb300 as giga
+    from paper_2504_01266_gb300 import _lib as L
+    shapes = workloads.ragged_shapes()
+    imgs, taps = [], 0
+    for idx, (h, w_, k) in enumerate(shapes):
+        g = workloads.generator("ragged", salt=idx + 1, device=str(dev))
+        x = torch.rand((3, h, w_), generator=g, device=dev)
+        wt = torch.randn((3, k, k), generator=g, device=dev) * 0.1
+        dy = torch.randn((3, h, w_), generator=g, device=dev)
+        imgs.append({"x": x, "dy": dy, "w": wt, "y": torch.empty_like(x),
+                     "dx": torch.empty_like(x), "dw": torch.empty((3, k, k), device=dev)})
+        taps += 3 * 3 * h * w_ * k * k
+    stream = torch.cuda.current_stream(dev)
+    plan = giga.BatchedPlan(imgs, 7, "zero")
+    plan.upload()
+    torch.cuda.synchronize(dev)
+    s = torch.cuda.Stream(dev)
+    s.wait_stream(stream)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(graph, stream=s):
+            plan.run()
+    torch.cuda.synchronize(dev)
+    ms_graph = _events(stream, graph.replay, iters)
+    sp = stream.cuda_stream
+    descs = [L.desc(1, 3, 3, im["x"].shape[1], im["x"].shape[2], im["w"].shape[-1], 3, 0,
+                    L.GIGA_F32, L.GIGA_LAYOUT_NCHW) for im in imgs]
+    wsb = max(L.giga_conv2d_workspace_size(d, 6) for d in descs)
+    ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+    ref_dy = [im["dx"].clone() for im in imgs[:4]]
+    ref_y = [im["y"].clone() for im in imgs[:4]]
+
+    def loop():
+        for d, im in zip(descs, imgs):
+            L.check(L.giga_conv2d_fwd(d, im["x"].data_ptr(), im["w"].data_ptr(),
+                                      im["y"].data_ptr(), None, 0, sp), "fwd")
+            L.check(L.giga_conv2d_bwd(d, im["x"].data_ptr(), im["dy"].data_ptr(),
+                                      im["w"].data_ptr(), im["dx"].data_ptr(),
+                                      im["dw"].data_ptr(), ws.data_ptr(), wsb, sp), "bwd")
+    ms_loop = _events(stream, loop, max(2, iters // 2))
+    same = all(torch.equal(a, im["y"]) and torch.equal(b, im["dx"])
+               for a, b, im in zip(ref_y, ref_dy, imgs[:4]))
+    plan.close()
+    px = sum(3 * h * w_ for h, w_, _ in shapes)
+    return {"workload": "256 images 3 x U[64,4096]^2, K in {3,5,9,11}, zero border, fwd+bwd",
+            "pixels": px, "graph_persistent": {"ms": ms_graph, "value": taps / (ms_graph * 1e-3) / 1e9},
+            "per_image_loop": {"ms": ms_loop, "value": taps / (ms_loop * 1e-3) / 1e9,
+                               "launches": 4 * len(imgs)},
+            "speedup": ms_loop / ms_graph,
+            "y_dx_bitwise_equal_to_per_image_path": bool(same)}
+
+
+def compare_dense(dev, iters, bf16_peak):
+    """Dense 3 x 3, 64 -> 64 channels, 8 x 1024 x 1024 BF16 NHWC on tcgen05:
+    forward, input gradient and filter gradient, TFLOP/s against the measured
+    BF16 peak, sampled error against the FP64 oracle."""
+    import torch
+    import oracle
+    import workloads
+    import paper_2504_01266_gb300 as giga
+    x, w, dy = workloads.dense()
+    xc, wc, dyc = x.to(dev), w.to(dev), dy.to(dev)
+    stream = torch.cuda.current_stream(dev)
+    y = torch.empty_like(xc)
+    dx = torch.empty_like(dyc)
+    dw = torch.empty((64, 3, 3, 64), device=dev)
+    flop = 2 * 8 * 1024 * 1024 * 64 * 64 * 9
+    res = {}
+    for name, fn in (("fwd", lambda: giga.dense_conv2d_fwd(xc, wc, out=y)),
+                     ("bwd_input", lambda: giga.dense_conv2d_bwd_input(dyc, wc, out=dx)),
+                     ("bwd_filter", lambda: giga.dense_conv2d_bwd_filter(xc, dyc, out=dw))):
+        ms = _events(stream, fn, iters)
+        tf = flop / (ms * 1e-3) / 1e12
+        res[name] = {"ms": ms, "tflops": tf, "frac_of_bf16_peak": tf / bf16_peak}
+    giga.check_device_error(dev)
+    idx = workloads.sample_indices(y.numel(), 1500, salt=11)
+    got = y.reshape(-1)[idx.to(dev)].double().cpu().numpy()
+    ref = oracle.dense_fwd_points(x.double().numpy(), w.double().numpy(), 0, idx.numpy())
+    res["fwd"]["err_normwise_sampled"] = _normwise(got, ref)
+    res["workload"] = "8x1024x1024x64 BF16 NHWC, 3x3 64->64 normal(0,0.05), zero border"
+    res["bytes_per_op"] = 2 * x.numel() * 2
+    return res
+
+
 # ------------------------------------------------------------------- GPU
 
 def run_giga(args):
@@ -357,6 +538,23 @@ def run_giga(args):
                "h2d_bytes_per_step": 2 * px * elem,
                "d2h_bytes_per_step": len(KS) * (2 * px * elem) + sum(C * K * K * 4 for K in KS)}
 
+    compare = None
+    if not args.no_compare:
+        del y, dx
+        torch.cuda.empty_cache()
+        bf16_peak = 1894.6
+        try:
+            with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+                bf16_peak = float(json.load(f)["bf16_tflops"])
+        except Exception:
+            pass
+        compare = {}
+        for name, fn in (("bf16", lambda: compare_bf16(dev, 5)),
+                         ("ragged", lambda: compare_ragged(dev, 5)),
+                         ("dense", lambda: compare_dense(dev, 10, bf16_peak))):
+            compare[name] = fn()
+            torch.cuda.empty_cache()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         v, cores, dt, desc = oracle_sample_rate(H, 2)
@@ -379,6 +577,7 @@ def run_giga(args):
             "gpu_launches": launches,
             "clocks": clocks.summary(),
             "ops": ops,
+            "compare": compare,
         }
         print(json.dumps(line))
     if world > 1:
@@ -396,6 +595,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="built-in default configurations")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip the BF16 / ragged / dense comparison measurements")
     ap.add_argument("--images", type=int, default=N,
                     help="images per GPU (profiling runs use 1: 201 MB per tensor, above L2)")
     args = ap.parse_args()
