@@ -586,6 +586,25 @@ def run_giga(args):
     return 0
 
 
+def run_section(args):
+    import torch
+    from paper_2504_01266_gb300 import build
+    build.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    peak = 1894.6
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peak = float(json.load(f)["bf16_tflops"])
+    except Exception:
+        pass
+    fn = {"bf16": lambda: compare_bf16(dev, args.steps),
+          "ragged": lambda: compare_ragged(dev, args.steps),
+          "dense": lambda: compare_dense(dev, args.steps, peak)}[args.section]
+    print(json.dumps({"section": args.section, "result": fn()}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -597,6 +616,8 @@ def main():
     ap.add_argument("--no-tune", action="store_true", help="built-in default configurations")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the BF16 / ragged / dense comparison measurements")
+    ap.add_argument("--section", choices=["bf16", "ragged", "dense"],
+                    help="run only this comparison and print its result (profiling aid)")
     ap.add_argument("--images", type=int, default=N,
                     help="images per GPU (profiling runs use 1: 201 MB per tensor, above L2)")
     args = ap.parse_args()
@@ -604,6 +625,8 @@ def main():
         set_images(args.images)
     if args.impl == "reference":
         return run_reference(args)
+    if args.section:
+        return run_section(args)
     return run_giga(args)
 
 

@@ -37,15 +37,12 @@ namespace giga {
 constexpr int kDenseC = 64;          // input and output channels
 constexpr int kDenseTaps = 9;        // 3 x 3
 constexpr int kDenseTileM = 128;     // output pixels per tile
-constexpr int kDenseStages = 6;
 constexpr int kDenseThreads = 192;
 constexpr int kDenseABytes = kDenseTileM * kDenseC * 2;  // 16 KB
 constexpr int kDenseBBytes = kDenseC * kDenseC * 2;      // 8 KB per tap
-constexpr int kDenseTmemCols = 128;
+constexpr int kDenseTmemCols = 256;
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // give up a wait after 2 s
 
-constexpr size_t kDenseSmem = 1024 /* alignment slack */ + kDenseTaps * kDenseBBytes +
-                              kDenseStages * kDenseABytes + 256;
 
 // error codes written to *err (first one wins)
 enum { kDenseErrNone = 0, kDenseErrTimeout = 1 };
@@ -111,6 +108,27 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
+__device__ __forceinline__ void tma_store_4d(const CUtensorMap* map, const void* src, int c0,
+                                             int c1, int c2, int c3) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.global.shared::cta.bulk_group [%0, {%2, %3, %4, %5}], [%1];" ::"l"(
+          reinterpret_cast<uint64_t>(map)),
+      "r"(s_addr(src)), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+      : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// Wait until at most N committed bulk stores still read their shared source.
+template <int N>
+__device__ __forceinline__ void bulk_wait_read() {
+  asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// Barrier among the 4 epilogue warps only (named barrier 1, 128 threads).
+__device__ __forceinline__ void epilogue_barrier() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
 __device__ __forceinline__ void tc_fence_before() {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
@@ -120,6 +138,9 @@ __device__ __forceinline__ void tc_fence_after() {
 
 // Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
 // 1024 bytes apart (stride byte offset), descriptor version 1.
+// The swizzle phase of each 128-byte row follows from its absolute shared
+// address, so a start address 128 * b bytes into a 1024-aligned band (a view
+// shifted by b pixels) needs no base offset.
 __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr >> 4) & 0x3FFF);
@@ -199,33 +220,58 @@ __device__ __forceinline__ void dense_fail(int* err, volatile int* abort_flag) {
   *abort_flag = 1;
 }
 
+// Work order: output-row tiles (n, strip jt, row i), i fastest; CTA b owns the
+// contiguous range [b*T/G, (b+1)*T/G).  A run of consecutive rows of one strip
+// needs input rows i0 - 1 .. i1 (130-pixel bands with the one-pixel halo on
+// each side), each loaded ONCE into a ring slot; output row i reads the bands
+// of rows i - 1, i, i + 1, and tap (a, b) is the band of row i + a - 1 viewed
+// from pixel b (a start address b * 128 bytes into the slot).
+constexpr int kBandPx = kDenseTileM + 2;              // 130 pixels
+constexpr int kBandBytes = kBandPx * kDenseC * 2;     // 16,640 bytes loaded
+constexpr int kSlotBytes = 17 * 1024;                 // 1024-aligned slot
+constexpr int kBandSlots = 6;
+constexpr int kAccBufs = 4;                            // TMEM accumulators (64 columns each)
+constexpr int kOutBufs = 2;                            // output staging tiles (16 KB each)
+constexpr size_t kDenseSmemBand = 1024 + kDenseTaps * kDenseBBytes + kBandSlots * kSlotBytes +
+                                  kOutBufs * kDenseABytes + 256;
+
+__device__ __forceinline__ void tile_range(int64_t total, int64_t& begin, int64_t& end) {
+  begin = total * blockIdx.x / gridDim.x;
+  end = total * (blockIdx.x + 1) / gridDim.x;
+}
+
 __global__ void __launch_bounds__(kDenseThreads, 1)
     dense_fwd_kernel(const __grid_constant__ CUtensorMap tmap_x,
-                     const __grid_constant__ CUtensorMap tmap_w, DenseParams p) {
+                     const __grid_constant__ CUtensorMap tmap_w,
+                     const __grid_constant__ CUtensorMap tmap_y, DenseParams p) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem =
       reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* sB = smem;
   uint8_t* sA = smem + kDenseTaps * kDenseBBytes;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sA + kDenseStages * kDenseABytes);
+  uint8_t* sOut = sA + kBandSlots * kSlotBytes;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sOut + kOutBufs * kDenseABytes);
   uint64_t* full = bars;
-  uint64_t* empty = bars + kDenseStages;
-  uint64_t* bfull = bars + 2 * kDenseStages;
-  uint64_t* tfull = bars + 2 * kDenseStages + 1;   // [2]
-  uint64_t* tempty = bars + 2 * kDenseStages + 3;  // [2]
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kDenseStages + 5);
+  uint64_t* empty = bars + kBandSlots;
+  uint64_t* bfull = bars + 2 * kBandSlots;
+  uint64_t* tfull = bars + 2 * kBandSlots + 1;              // [kAccBufs]
+  uint64_t* tempty = bars + 2 * kBandSlots + 1 + kAccBufs;  // [kAccBufs]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kBandSlots + 1 + 2 * kAccBufs);
   __shared__ volatile int s_abort;
+  __shared__ volatile int s_go;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int64_t t_begin, t_end;
+  tile_range(p.num_tiles, t_begin, t_end);
 
   if (threadIdx.x == 0) {
     s_abort = 0;
-    for (int s = 0; s < kDenseStages; ++s) {
+    for (int s = 0; s < kBandSlots; ++s) {
       mbar_init(full + s, 1);
       mbar_init(empty + s, 1);
     }
     mbar_init(bfull, 1);
-    for (int a = 0; a < 2; ++a) {
+    for (int a = 0; a < kAccBufs; ++a) {
       mbar_init(tfull + a, 1);
       mbar_init(tempty + a, 4 * 32);
     }
@@ -250,27 +296,25 @@ __global__ void __launch_bounds__(kDenseThreads, 1)
       mbar_expect_tx(bfull, kDenseTaps * kDenseBBytes);
       for (int t = 0; t < kDenseTaps; ++t)
         tma_load_2d(sB + t * kDenseBBytes, &tmap_w, t * kDenseC, 0, bfull);
-      int stage = 0;
-      uint32_t phase = 0;
-      for (int64_t tile = blockIdx.x; tile < p.num_tiles && !s_abort; tile += gridDim.x) {
-        const int jt = (int)(tile % p.tiles_w);
-        const int64_t r = tile / p.tiles_w;
-        const int i = (int)(r % p.H);
-        const int n = (int)(r / p.H);
-        const int j0 = jt * kDenseTileM;
-        for (int t = 0; t < kDenseTaps; ++t) {
-          if (!mbar_wait(empty + stage, phase ^ 1)) {
+      uint32_t seq = 0;  // global band-load counter: slot seq % S, phase (seq / S) & 1
+      for (int64_t tile = t_begin; tile < t_end && !s_abort;) {
+        // a run of rows of one strip: [tile, run_end)
+        const int i0 = (int)(tile % p.H);
+        const int64_t strip = tile / p.H;  // n * tiles_w + jt
+        const int64_t run_end = min(t_end, (strip + 1) * (int64_t)p.H);
+        const int i1 = i0 + (int)(run_end - tile);
+        const int jt = (int)(strip % p.tiles_w);
+        const int n = (int)(strip / p.tiles_w);
+        for (int r = i0 - 1; r <= i1 && !s_abort; ++r, ++seq) {
+          const int slot = (int)(seq % kBandSlots);
+          if (!mbar_wait(empty + slot, ((seq / kBandSlots) & 1) ^ 1)) {
             dense_fail(p.err, &s_abort);
             break;
           }
-          mbar_expect_tx(full + stage, kDenseABytes);
-          tma_load_4d(sA + stage * kDenseABytes, &tmap_x, 0, j0 + t % 3 - 1, i + t / 3 - 1, n,
-                      full + stage);
-          if (++stage == kDenseStages) {
-            stage = 0;
-            phase ^= 1;
-          }
+          mbar_expect_tx(full + slot, kBandBytes);
+          tma_load_4d(sA + slot * kSlotBytes, &tmap_x, 0, jt * kDenseTileM - 1, r, n, full + slot);
         }
+        tile = run_end;
       }
     }
   } else if (warp == 1) {
@@ -278,57 +322,84 @@ __global__ void __launch_bounds__(kDenseThreads, 1)
       // ------------------------------------------------------- MMA issuer
       bool ok = mbar_wait(bfull, 0);
       if (!ok) dense_fail(p.err, &s_abort);
-      int stage = 0;
-      uint32_t phase = 0;
+      uint32_t seq = 0;  // band counter of the first band of the current run
       int acc = 0;
       uint32_t acc_phase = 0;
       const uint32_t b_base = s_addr(sB);
-      for (int64_t tile = blockIdx.x; ok && tile < p.num_tiles && !s_abort; tile += gridDim.x) {
-        if (!mbar_wait(tempty + acc, acc_phase ^ 1)) {
-          dense_fail(p.err, &s_abort);
-          break;
-        }
-        tc_fence_after();
-        const uint32_t d_tmem = tmem_base + (uint32_t)(acc * 64);
-        for (int t = 0; t < kDenseTaps; ++t) {
-          if (!mbar_wait(full + stage, phase)) {
+      const uint32_t a_base = s_addr(sA);
+      for (int64_t tile = t_begin; ok && tile < t_end && !s_abort;) {
+        const int i0 = (int)(tile % p.H);
+        const int64_t strip = tile / p.H;
+        const int64_t run_end = min(t_end, (strip + 1) * (int64_t)p.H);
+        const int rows = (int)(run_end - tile);
+        // bands of this run: seq .. seq + rows + 1 (rows i0 - 1 .. i0 + rows)
+        for (int k = 0; k < rows && ok; ++k) {
+          // output row i0 + k uses bands seq + k, seq + k + 1, seq + k + 2;
+          // wait for the newest ones (the oldest were waited for earlier)
+          for (int q = (k == 0 ? 0 : 2); q < 3; ++q) {
+            const uint32_t b = seq + k + q;
+            if (!mbar_wait(full + b % kBandSlots, (b / kBandSlots) & 1)) {
+              dense_fail(p.err, &s_abort);
+              ok = false;
+              break;
+            }
+          }
+          if (!ok) break;
+          if (!mbar_wait(tempty + acc, acc_phase ^ 1)) {
             dense_fail(p.err, &s_abort);
             ok = false;
             break;
           }
           tc_fence_after();
-          const uint32_t a_base = s_addr(sA + stage * kDenseABytes);
+          const uint32_t d_tmem = tmem_base + (uint32_t)(acc * 64);
 #pragma unroll
-          for (int k = 0; k < kDenseC / 16; ++k) {
-            tc_mma(d_tmem, sw128_desc(a_base + 32 * k),
-                   sw128_desc(b_base + t * kDenseBBytes + 32 * k), kDenseIdesc,
-                   (t > 0 || k > 0) ? 1u : 0u);
+          for (int t = 0; t < kDenseTaps; ++t) {
+            const uint32_t band = seq + k + t / 3;
+            const uint32_t a_row = a_base + (band % kBandSlots) * kSlotBytes + (t % 3) * 128;
+#pragma unroll
+            for (int kk = 0; kk < kDenseC / 16; ++kk)
+              tc_mma(d_tmem, sw128_desc(a_row + 32 * kk),
+                     sw128_desc(b_base + t * kDenseBBytes + 32 * kk), kDenseIdesc,
+                     (t > 0 || kk > 0) ? 1u : 0u);
           }
-          tc_commit(empty + stage);  // frees the stage once these MMAs finish
-          if (++stage == kDenseStages) {
-            stage = 0;
-            phase ^= 1;
+          // the band of row i0 + k - 1 is not read again in this run
+          tc_commit(empty + (seq + k) % kBandSlots);
+          tc_commit(tfull + acc);
+          if (++acc == kAccBufs) {
+            acc = 0;
+            acc_phase ^= 1;
           }
         }
         if (!ok) break;
-        tc_commit(tfull + acc);  // accumulator ready for the epilogue
-        if (++acc == 2) {
-          acc = 0;
-          acc_phase ^= 1;
-        }
+        // release the run's last two bands
+        tc_commit(empty + (seq + rows) % kBandSlots);
+        tc_commit(empty + (seq + rows + 1) % kBandSlots);
+        seq += rows + 2;
+        tile = run_end;
       }
     }
   } else {
     // ------------------------------------------------------------ epilogue
+    // TMEM -> registers -> BF16 row of one pixel -> 128-byte-swizzled staging
+    // tile in shared memory (conflict-free) -> one TMA tensor store per tile.
     const int quad = warp & 3;  // TMEM lane quadrant this warp may access
     const int row = quad * 32 + lane;
-    int acc = 0;
+    const bool leader = (warp == 2 && lane == 0);
+    int acc = 0, ob = 0;
     uint32_t acc_phase = 0;
-    for (int64_t tile = blockIdx.x; tile < p.num_tiles && !s_abort; tile += gridDim.x) {
-      if (!mbar_wait(tfull + acc, acc_phase)) {
-        dense_fail(p.err, &s_abort);
-        break;
+    for (int64_t tile = t_begin; tile < t_end; ++tile) {
+      // The leader alone does the bounded waits and broadcasts the outcome, so
+      // the four warps leave the loop together (they share a named barrier).
+      if (leader) {
+        int ok = !s_abort && mbar_wait(tfull + acc, acc_phase);
+        if (!ok) dense_fail(p.err, &s_abort);
+        // staging buffer ob is free once the store issued from it two tiles
+        // ago has finished reading it
+        else bulk_wait_read<kOutBufs - 1>();
+        s_go = ok;
       }
+      epilogue_barrier();
+      if (!s_go) break;
       tc_fence_after();
       const uint32_t taddr = tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(acc * 64);
       float v[64];
@@ -342,33 +413,41 @@ __global__ void __launch_bounds__(kDenseThreads, 1)
       tc_wait_ld();
       tc_fence_before();
       mbar_arrive(tempty + acc);
-      const int jt = (int)(tile % p.tiles_w);
-      const int64_t r = tile / p.tiles_w;  // n * H + i
-      const int j = jt * kDenseTileM + row;
-      if (j < p.W) {
-        uint4* dst = reinterpret_cast<uint4*>(p.y + ((r * p.W + j) * kDenseC));
+      uint8_t* out_row = sOut + ob * kDenseABytes + row * 128;
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          uint4 u;
-          __nv_bfloat162 h0 = __floats2bfloat162_rn(v[8 * q + 0], v[8 * q + 1]);
-          __nv_bfloat162 h1 = __floats2bfloat162_rn(v[8 * q + 2], v[8 * q + 3]);
-          __nv_bfloat162 h2 = __floats2bfloat162_rn(v[8 * q + 4], v[8 * q + 5]);
-          __nv_bfloat162 h3 = __floats2bfloat162_rn(v[8 * q + 6], v[8 * q + 7]);
-          u.x = *reinterpret_cast<uint32_t*>(&h0);
-          u.y = *reinterpret_cast<uint32_t*>(&h1);
-          u.z = *reinterpret_cast<uint32_t*>(&h2);
-          u.w = *reinterpret_cast<uint32_t*>(&h3);
-          dst[q] = u;
-        }
+      for (int q = 0; q < 8; ++q) {
+        uint4 u;
+        __nv_bfloat162 h0 = __floats2bfloat162_rn(v[8 * q + 0], v[8 * q + 1]);
+        __nv_bfloat162 h1 = __floats2bfloat162_rn(v[8 * q + 2], v[8 * q + 3]);
+        __nv_bfloat162 h2 = __floats2bfloat162_rn(v[8 * q + 4], v[8 * q + 5]);
+        __nv_bfloat162 h3 = __floats2bfloat162_rn(v[8 * q + 6], v[8 * q + 7]);
+        u.x = *reinterpret_cast<uint32_t*>(&h0);
+        u.y = *reinterpret_cast<uint32_t*>(&h1);
+        u.z = *reinterpret_cast<uint32_t*>(&h2);
+        u.w = *reinterpret_cast<uint32_t*>(&h3);
+        // 128-byte swizzle: 16-byte chunk q of row r lives at chunk q ^ (r % 8)
+        *reinterpret_cast<uint4*>(out_row + ((q ^ (row & 7)) << 4)) = u;
       }
-      if (++acc == 2) {
+      fence_proxy_async();
+      epilogue_barrier();
+      if (leader) {
+        const int i = (int)(tile % p.H);
+        const int64_t strip = tile / p.H;
+        const int jt = (int)(strip % p.tiles_w);
+        const int n = (int)(strip / p.tiles_w);
+        tma_store_4d(&tmap_y, sOut + ob * kDenseABytes, 0, jt * kDenseTileM, i, n);
+        bulk_commit();
+      }
+      ob ^= 1;
+      if (++acc == kAccBufs) {
         acc = 0;
         acc_phase ^= 1;
       }
     }
+    if (leader) bulk_wait_all();
   }
 
-  // Drain: the MMA issuer's last commits must land before TMEM is freed.
+  // Drain: every MMA was waited for by the epilogue (tfull) before this point.
   tc_fence_before();
   __syncthreads();
   if (warp == 1) {
@@ -681,18 +760,10 @@ cudaError_t dense_launch(const void* x, const void* w, void* y, int64_t N, int64
     if (e != cudaSuccess) return e;
     wk = ws;
   }
-  CUtensorMap tx, tw;
-  {
-    cuuint64_t dims[4] = {(cuuint64_t)kDenseC, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)N};
-    cuuint64_t strides[3] = {(cuuint64_t)kDenseC * 2, (cuuint64_t)W * kDenseC * 2,
-                             (cuuint64_t)H * W * kDenseC * 2};
-    cuuint32_t box[4] = {(cuuint32_t)kDenseC, (cuuint32_t)kDenseTileM, 1, 1};
-    cuuint32_t estr[4] = {1, 1, 1, 1};
-    if (enc(&tx, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(x), dims, strides, box,
-            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-      return cudaErrorInvalidValue;
-  }
+  CUtensorMap tx, tw, ty;
+  if (!make_nhwc_map(enc, &tx, x, N, H, W, kBandPx) ||
+      !make_nhwc_map(enc, &ty, y, N, H, W, kDenseTileM))
+    return cudaErrorInvalidValue;
   {
     cuuint64_t dims[2] = {(cuuint64_t)kDenseTaps * kDenseC, (cuuint64_t)kDenseC};
     cuuint64_t strides[1] = {(cuuint64_t)kDenseTaps * kDenseC * 2};
@@ -706,7 +777,7 @@ cudaError_t dense_launch(const void* x, const void* w, void* y, int64_t N, int64
   int* err = nullptr;
   cudaError_t e = cudaGetSymbolAddress(reinterpret_cast<void**>(&err), g_dense_err);
   if (e != cudaSuccess) return e;
-  e = set_smem_once<dense_fwd_kernel>(kDenseSmem);
+  e = set_smem_once<dense_fwd_kernel>(kDenseSmemBand);
   if (e != cudaSuccess) return e;
   DenseParams prm;
   prm.y = static_cast<__nv_bfloat16*>(y);
@@ -720,7 +791,7 @@ cudaError_t dense_launch(const void* x, const void* w, void* y, int64_t N, int64
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int grid = (int)std::min<int64_t>(prm.num_tiles, (int64_t)(sms > 0 ? sms : 148));
-  dense_fwd_kernel<<<grid, kDenseThreads, kDenseSmem, st>>>(tx, tw, prm);
+  dense_fwd_kernel<<<grid, kDenseThreads, kDenseSmemBand, st>>>(tx, tw, ty, prm);
   note_launch();
   return cudaGetLastError();
 }
