@@ -411,8 +411,16 @@ struct BwdShape {
 
 __device__ __forceinline__ int group_lo(int g, int K, int GT) { return g * K / GT; }
 
+// CTAs per SM the backward kernel is compiled for: the small-K instances are
+// memory-bound and need fewer registers, so a third CTA adds loads in flight.
+// (BF16 staging keeps more values live, so it stays at two.)
+template <typename T, int K>
+constexpr int bwd_min_ctas() {
+  return (K == 1 || (K <= 5 && sizeof(T) == 4)) ? 3 : 2;
+}
+
 template <typename T, int K, int MODE>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, bwd_min_ctas<T, K>())
     dw_bwd_kernel(const T* __restrict__ x, const T* __restrict__ dy, const float* __restrict__ w,
                   T* __restrict__ dx, float* __restrict__ partials, int C, int H, int W,
                   int tiles_x, int tiles_per_plane, int chunks_per_plane, int tpc, int clamp,
