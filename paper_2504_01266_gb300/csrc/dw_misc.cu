@@ -28,8 +28,152 @@ __global__ void dw_fixup_kernel(const T* __restrict__ dy, const float* __restric
   }
 }
 
+// ---- FP32 clamp fold as corrections on top of the zero-border values g that
+// the tile pass already wrote.  With g[u][v] = sum_{a,b} w[a][b] dy[u-a+r][v-b+r]
+// (dy zero outside) on the extended domain, the clamp adjoint is
+// dx[p][q] = sum_{u: B(u)=p} sum_{v: B(v)=q} g[u][v], i.e. g plus the margin sums
+//   top     T[q] = sum_{i<r}  sum_b Wt[i][b] dy[i][q-b+r],     Wt[i][b] = sum_{a<=r-1-i} w[a][b]
+//   bottom  B[q] = sum_{d<r}  sum_b Wb[d][b] dy[H-1-d][q-b+r], Wb[d][b] = sum_{a>=r+1+d} w[a][b]
+//   left    L[p] = sum_{j<r}  sum_a Wl[j][a] dy[p-a+r][j],     Wl[j][a] = sum_{b<=r-1-j} w[a][b]
+//   right   R[p] = sum_{e<r}  sum_a Wr[e][a] dy[p-a+r][W-1-e], Wr[e][a] = sum_{b>=r+1+e} w[a][b]
+// and at the corners the doubly-folded sums, e.g.
+//   TL = sum_{i<r,j<r} (sum_{a<=r-1-i} sum_{b<=r-1-j} w[a][b]) dy[i][j]
+// (i, d < H and j, e < W; dy outside the image reads zero).  The row kernel adds
+// T and B to the first and last row; the column kernel, launched after it,
+// adds L, R and the corner sums to the first and last column.
+constexpr int kFoldThreads = 256;
+
+__device__ __forceinline__ float dy_at(const float* g, int H, int W, int i, int j) {
+  return (i >= 0 && i < H && j >= 0 && j < W) ? g[(int64_t)i * W + j] : 0.f;
+}
+
+__global__ void dw_fold_rows_kernel(const float* __restrict__ dy, const float* __restrict__ w,
+                                    float* __restrict__ dx, int C, int H, int W, int K) {
+  extern __shared__ float tab[];  // Wt[r][K], Wb[r][K]
+  const int r = (K - 1) / 2;
+  const int64_t plane = blockIdx.y;
+  const float* f = w + (plane % C) * (int64_t)K * K;
+  float* Wt = tab;
+  float* Wb = tab + r * K;
+  for (int k = threadIdx.x; k < r * K; k += blockDim.x) {
+    const int i = k / K, b = k % K;
+    float t = 0.f, u = 0.f;
+    for (int a = 0; a <= r - 1 - i; ++a) t += f[a * K + b];
+    for (int a = r + 1 + i; a < K; ++a) u += f[a * K + b];
+    Wt[k] = t;
+    Wb[k] = u;
+  }
+  __syncthreads();
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= W) return;
+  const float* g = dy + plane * (int64_t)H * W;
+  const int rows = min(r, H);
+  float top = 0.f, bot = 0.f;
+  for (int i = 0; i < rows; ++i)
+    for (int b = 0; b < K; ++b) {
+      top = fmaf(Wt[i * K + b], dy_at(g, H, W, i, q - b + r), top);
+      bot = fmaf(Wb[i * K + b], dy_at(g, H, W, H - 1 - i, q - b + r), bot);
+    }
+  float* d = dx + plane * (int64_t)H * W;
+  if (H == 1) {
+    d[q] += top + bot;
+  } else {
+    d[q] += top;
+    d[(int64_t)(H - 1) * W + q] += bot;
+  }
+}
+
+__global__ void dw_fold_cols_kernel(const float* __restrict__ dy, const float* __restrict__ w,
+                                    float* __restrict__ dx, int C, int H, int W, int K) {
+  extern __shared__ float tab[];  // Wl[r][K], Wr[r][K], corners 4 x r x r
+  const int r = (K - 1) / 2;
+  const int64_t plane = blockIdx.y;
+  const float* f = w + (plane % C) * (int64_t)K * K;
+  float* Wl = tab;
+  float* Wr = tab + r * K;
+  float* Ctl = tab + 2 * r * K;
+  float* Ctr = Ctl + r * r;
+  float* Cbl = Ctr + r * r;
+  float* Cbr = Cbl + r * r;
+  for (int k = threadIdx.x; k < r * K; k += blockDim.x) {
+    const int j = k / K, a = k % K;
+    float l = 0.f, rr = 0.f;
+    for (int b = 0; b <= r - 1 - j; ++b) l += f[a * K + b];
+    for (int b = r + 1 + j; b < K; ++b) rr += f[a * K + b];
+    Wl[k] = l;
+    Wr[k] = rr;
+  }
+  for (int k = threadIdx.x; k < r * r; k += blockDim.x) {
+    const int i = k / r, j = k % r;
+    float tl = 0.f, tr = 0.f, bl = 0.f, br = 0.f;
+    for (int a = 0; a < K; ++a)
+      for (int b = 0; b < K; ++b) {
+        const float v = f[a * K + b];
+        const bool top = a <= r - 1 - i, bottom = a >= r + 1 + i;
+        const bool left = b <= r - 1 - j, right = b >= r + 1 + j;
+        if (top && left) tl += v;
+        if (top && right) tr += v;
+        if (bottom && left) bl += v;
+        if (bottom && right) br += v;
+      }
+    Ctl[k] = tl;
+    Ctr[k] = tr;
+    Cbl[k] = bl;
+    Cbr[k] = br;
+  }
+  __syncthreads();
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= H) return;
+  const float* g = dy + plane * (int64_t)H * W;
+  const int cols = min(r, W), rows = min(r, H);
+  float left = 0.f, right = 0.f;
+  for (int j = 0; j < cols; ++j)
+    for (int a = 0; a < K; ++a) {
+      left = fmaf(Wl[j * K + a], dy_at(g, H, W, p - a + r, j), left);
+      right = fmaf(Wr[j * K + a], dy_at(g, H, W, p - a + r, W - 1 - j), right);
+    }
+  // corner sums belong to the pixels of the first / last row
+  if (p == 0 || p == H - 1) {
+    for (int i = 0; i < rows; ++i)
+      for (int j = 0; j < cols; ++j) {
+        if (p == 0) {
+          left = fmaf(Ctl[i * r + j], dy_at(g, H, W, i, j), left);
+          right = fmaf(Ctr[i * r + j], dy_at(g, H, W, i, W - 1 - j), right);
+        }
+        if (p == H - 1) {
+          left = fmaf(Cbl[i * r + j], dy_at(g, H, W, H - 1 - i, j), left);
+          right = fmaf(Cbr[i * r + j], dy_at(g, H, W, H - 1 - i, W - 1 - j), right);
+        }
+      }
+  }
+  float* d = dx + plane * (int64_t)H * W + (int64_t)p * W;
+  if (W == 1) {
+    d[0] += left + right;
+  } else {
+    d[0] += left;
+    d[W - 1] += right;
+  }
+}
+
 cudaError_t dw_fixup_launch(const DwArgs& a, cudaStream_t st) {
   if (a.border != 1 || a.N * a.C * a.H * a.W == 0) return cudaSuccess;
+  const int r = (a.K - 1) / 2;
+  if (a.dtype == 0 && r > 0 && a.N * a.C <= 65535) {
+    const int64_t planes = a.N * a.C;
+    const dim3 grid_rows((unsigned)((a.W + kFoldThreads - 1) / kFoldThreads), (unsigned)planes);
+    const dim3 grid_cols((unsigned)((a.H + kFoldThreads - 1) / kFoldThreads), (unsigned)planes);
+    dw_fold_rows_kernel<<<grid_rows, kFoldThreads, sizeof(float) * 2 * r * a.K, st>>>(
+        static_cast<const float*>(a.dy), a.w, static_cast<float*>(a.dx), (int)a.C, (int)a.H,
+        (int)a.W, a.K);
+    note_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    dw_fold_cols_kernel<<<grid_cols, kFoldThreads, sizeof(float) * (2 * r * a.K + 4 * r * r),
+                          st>>>(static_cast<const float*>(a.dy), a.w, static_cast<float*>(a.dx),
+                                (int)a.C, (int)a.H, (int)a.W, a.K);
+    note_launch();
+    return cudaGetLastError();
+  }
   const int64_t H = a.H, W = a.W;
   const int64_t edge = edge_pixels(H, W);
   const int64_t total = a.N * a.C * edge;
