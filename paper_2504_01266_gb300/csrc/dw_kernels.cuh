@@ -10,11 +10,12 @@
 //   dw[c][a][b]    = sum_{n,i,j} dy[n][c][i][j] * x~[n][c][i + a - r][j + b - r]
 //
 // Design (one CTA of 8 warps per 64 x 128 or 32 x 128 output tile):
-//  * The input tile and its halo are staged once into shared memory as FP32
-//    (BF16 storage is widened while staging) with 128-bit coalesced loads; the
-//    border rule is applied while staging, so the compute loops never branch
-//    on coordinates.  The column halo is rounded up to 4 so every staged row
-//    stays 16-byte aligned.
+//  * The input tile and its halo are staged once into shared memory in the
+//    storage type (FP32 or BF16) with asynchronous cp.async copies; the border
+//    rule is applied while staging, so the compute loops never branch on
+//    coordinates.  BF16 is widened to FP32 when a row enters registers.  The
+//    column halo is rounded up to 4 so every staged row stays 16-byte (FP32)
+//    or 8-byte (BF16) aligned.
 //  * Each lane owns 4 adjacent output columns and PY rows.  The filter is
 //    consumed A rows at a time with those A rows held in registers; every
 //    staged input row is read once per group with 128-bit shared loads and
@@ -36,7 +37,7 @@ template <int K>
 struct Geo {
   static constexpr int R = (K - 1) / 2;
   static constexpr int RP = (R + 3) / 4 * 4;        // column halo rounded up to 4
-  static constexpr int SP = kTileW + 2 * RP;        // staged row pitch (floats)
+  static constexpr int SP = kTileW + 2 * RP;        // staged row pitch (elements)
   static constexpr int OFF = RP - R;                // first column a lane needs
   static constexpr int NV = (OFF + K + 2) / 4 + 1;  // float4 loads per lane per row
   static constexpr int KP = (K + 3) / 4 * 4;         // staged filter row pitch
@@ -74,6 +75,11 @@ __device__ __forceinline__ void cp_async4(float* dst, const void* src, bool vali
                "r"(valid ? 4 : 0)
                : "memory");
 }
+__device__ __forceinline__ void cp_async8(void* dst, const void* src, bool valid) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(smem_addr(dst)), "l"(src),
+               "r"(valid ? 8 : 0)
+               : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
@@ -92,6 +98,42 @@ __device__ __forceinline__ float4 lds128_pinned(const float* p) {
                : "r"(smem_addr(p)));
   return v;
 }
+
+// Shared-memory tile element access: 4 consecutive staged elements -> FP32.
+template <typename T> struct Tile;
+template <> struct Tile<float> {
+  static __device__ __forceinline__ float4 load4(const float* p) {
+    return *reinterpret_cast<const float4*>(p);
+  }
+  static __device__ __forceinline__ float4 load4_pinned(const float* p) { return lds128_pinned(p); }
+  static __device__ __forceinline__ void store4(float* p, float4 v) {
+    *reinterpret_cast<float4*>(p) = v;
+  }
+};
+__device__ __forceinline__ float4 bf16x4_to_float4(uint32_t lo, uint32_t hi) {
+  return make_float4(__uint_as_float(lo << 16), __uint_as_float(lo & 0xffff0000u),
+                     __uint_as_float(hi << 16), __uint_as_float(hi & 0xffff0000u));
+}
+template <> struct Tile<__nv_bfloat16> {
+  static __device__ __forceinline__ float4 load4(const __nv_bfloat16* p) {
+    const uint2 u = *reinterpret_cast<const uint2*>(p);
+    return bf16x4_to_float4(u.x, u.y);
+  }
+  static __device__ __forceinline__ float4 load4_pinned(const __nv_bfloat16* p) {
+    uint32_t lo, hi;
+    asm volatile("ld.shared.v2.b32 {%0, %1}, [%2];" : "=r"(lo), "=r"(hi) : "r"(smem_addr(p)));
+    return bf16x4_to_float4(lo, hi);
+  }
+  // values come from BF16 storage, so the round trip is exact
+  static __device__ __forceinline__ void store4(__nv_bfloat16* p, float4 v) {
+    __nv_bfloat162 a = __floats2bfloat162_rn(v.x, v.y);
+    __nv_bfloat162 b = __floats2bfloat162_rn(v.z, v.w);
+    uint2 u;
+    u.x = *reinterpret_cast<uint32_t*>(&a);
+    u.y = *reinterpret_cast<uint32_t*>(&b);
+    *reinterpret_cast<uint2*>(p) = u;
+  }
+};
 
 // One staged chunk of 4 consecutive columns at (gi, gj..gj+3), border applied.
 template <typename T>
@@ -126,38 +168,38 @@ __device__ __forceinline__ float4 load_chunk(const T* __restrict__ plane, int H,
 }
 
 // Stage rows [ty0 - HR, ty0 - HR + rows) x cols [tx0 - HC, tx0 - HC + pitch)
-// of one image plane into shared memory as FP32.  Outside the image: zero, or
-// (clamp) the nearest edge pixel, row and column clamped independently.
-// FP32 storage: asynchronous cp.async copies (16 bytes where the chunk is
-// inside the image and aligned, 4 bytes otherwise; zero fill for the zero
-// border), so every copy of the tile is in flight at once.  BF16 storage:
-// 4 chunks per thread are loaded before any is stored (widened to FP32).
-// Completion: stage_wait().
+// of one image plane into shared memory (same element type as the tensor).
+// Outside the image: zero, or (clamp) the nearest edge pixel, row and column
+// clamped independently.  Chunks of 4 elements that lie inside the image on
+// an aligned row are asynchronous cp.async copies (16 bytes FP32, 8 bytes
+// BF16); rows outside a zero border are zero-filled by cp.async; the rest
+// (edges, clamped columns, unaligned rows) go element by element (FP32:
+// 4-byte cp.async; BF16: a plain load and store).  Completion: stage_wait().
 template <typename T, int HR, int HC, int PITCH, int NT = kThreads>
-__device__ __forceinline__ void stage_tile(float* __restrict__ sm, const T* __restrict__ plane,
+__device__ __forceinline__ void stage_tile(T* __restrict__ sm, const T* __restrict__ plane,
                                            int H, int W, int ty0, int tx0, int rows,
                                            bool clamp, bool vec) {
   constexpr int CPR = PITCH / 4;
   const int total = rows * CPR;
-  if constexpr (sizeof(T) == 4) {
-    for (int k = threadIdx.x; k < total; k += NT) {
-      const int sr = k / CPR;
-      const int sc = (k - sr * CPR) * 4;
-      int gi = ty0 - HR + sr;
-      const int gj = tx0 - HC + sc;
-      float* dst = sm + sr * PITCH + sc;
-      bool row_ok = gi >= 0 && gi < H;
-      if (!row_ok && clamp) {
-        gi = gi < 0 ? 0 : H - 1;
-        row_ok = true;
-      }
+  for (int k = threadIdx.x; k < total; k += NT) {
+    const int sr = k / CPR;
+    const int sc = (k - sr * CPR) * 4;
+    int gi = ty0 - HR + sr;
+    const int gj = tx0 - HC + sc;
+    T* dst = sm + sr * PITCH + sc;
+    bool row_ok = gi >= 0 && gi < H;
+    if (!row_ok && clamp) {
+      gi = gi < 0 ? 0 : H - 1;
+      row_ok = true;
+    }
+    if constexpr (sizeof(T) == 4) {
       if (!row_ok) {
-        cp_async16(dst, plane, false);
+        cp_async16(reinterpret_cast<float*>(dst), plane, false);
         continue;
       }
       const T* src = plane + (int64_t)gi * W;
       if (vec && gj >= 0 && gj + 3 < W) {
-        cp_async16(dst, src + gj, true);
+        cp_async16(reinterpret_cast<float*>(dst), src + gj, true);
       } else {
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -167,35 +209,23 @@ __device__ __forceinline__ void stage_tile(float* __restrict__ sm, const T* __re
             j = j < 0 ? 0 : W - 1;
             ok = true;
           }
-          cp_async4(dst + q, ok ? src + j : plane, ok);
+          cp_async4(reinterpret_cast<float*>(dst) + q, ok ? src + j : plane, ok);
         }
       }
-    }
-    cp_async_commit();
-  } else {
-    constexpr int U = 4;
-    for (int k0 = threadIdx.x; k0 < total; k0 += U * NT) {
-      float4 v[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int k = k0 + u * NT;
-        if (k < total) {
-          const int sr = k / CPR;
-          const int sc = (k - sr * CPR) * 4;
-          v[u] = load_chunk<T>(plane, H, W, ty0 - HR + sr, tx0 - HC + sc, clamp, vec);
-        }
+    } else {
+      if (!row_ok) {
+        cp_async8(dst, plane, false);
+        continue;
       }
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int k = k0 + u * NT;
-        if (k < total) {
-          const int sr = k / CPR;
-          const int sc = (k - sr * CPR) * 4;
-          *reinterpret_cast<float4*>(sm + sr * PITCH + sc) = v[u];
-        }
+      const T* src = plane + (int64_t)gi * W;
+      if (vec && gj >= 0 && gj + 3 < W) {
+        cp_async8(dst, src + gj, true);
+      } else {
+        Tile<T>::store4(dst, load_chunk<T>(plane, H, W, gi, gj, clamp, vec));
       }
     }
   }
+  cp_async_commit();
 }
 
 // Stage a K x K filter with rows padded to KP (zeros), optionally rotated by
@@ -229,12 +259,12 @@ __device__ __forceinline__ void store_block(T* __restrict__ plane, int H, int W,
   }
 }
 
-template <int K>
-__device__ __forceinline__ void load_window_row(const float* __restrict__ row,
+template <int K, typename TS>
+__device__ __forceinline__ void load_window_row(const TS* __restrict__ row,
                                                 float (&buf)[4 * Geo<K>::NV]) {
 #pragma unroll
   for (int v = 0; v < Geo<K>::NV; ++v) {
-    const float4 t = *reinterpret_cast<const float4*>(row + 4 * v);
+    const float4 t = Tile<TS>::load4(row + 4 * v);
     buf[4 * v + 0] = t.x;
     buf[4 * v + 1] = t.y;
     buf[4 * v + 2] = t.z;
@@ -245,8 +275,8 @@ __device__ __forceinline__ void load_window_row(const float* __restrict__ row,
 // acc[py][px] += sum_{s < A, b < K} f[s*KP + b] * win[(py + s) * SP + OFF + px + b]
 // `win` points at the staged row of output row 0 plus filter row 0 of this
 // group, at the lane's first column; `f` at filter row 0 of this group.
-template <int K, int PY, int A>
-__device__ __forceinline__ void fwd_group(const float* __restrict__ win,
+template <int K, int PY, int A, typename TS>
+__device__ __forceinline__ void fwd_group(const TS* __restrict__ win,
                                           const float* __restrict__ f, float (&acc)[PY][4]) {
   using G = Geo<K>;
   float wr[A][G::KP];
@@ -263,7 +293,7 @@ __device__ __forceinline__ void fwd_group(const float* __restrict__ win,
 #pragma unroll
   for (int ir = 0; ir < PY + A - 1; ++ir) {
     float buf[4 * G::NV];
-    load_window_row<K>(win + ir * G::SP, buf);
+    load_window_row<K, TS>(win + ir * G::SP, buf);
 #pragma unroll
     for (int s = 0; s < A; ++s) {
       const int py = ir - s;
@@ -278,8 +308,8 @@ __device__ __forceinline__ void fwd_group(const float* __restrict__ win,
   }
 }
 
-template <int K, int PY>
-__device__ __forceinline__ void fwd_block(const float* __restrict__ win,
+template <int K, int PY, typename TS>
+__device__ __forceinline__ void fwd_block(const TS* __restrict__ win,
                                           const float* __restrict__ f, float (&acc)[PY][4]) {
   constexpr int A = fwd_group_rows<K>();
   constexpr int NG = K / A;
@@ -290,24 +320,24 @@ __device__ __forceinline__ void fwd_block(const float* __restrict__ win,
     for (int px = 0; px < 4; ++px) acc[py][px] = 0.f;
 #pragma unroll 1
   for (int g = 0; g < NG; ++g)
-    fwd_group<K, PY, A>(win + g * A * Geo<K>::SP, f + g * A * Geo<K>::KP, acc);
+    fwd_group<K, PY, A, TS>(win + g * A * Geo<K>::SP, f + g * A * Geo<K>::KP, acc);
   if constexpr (REM > 0)
-    fwd_group<K, PY, REM>(win + NG * A * Geo<K>::SP, f + NG * A * Geo<K>::KP, acc);
+    fwd_group<K, PY, REM, TS>(win + NG * A * Geo<K>::SP, f + NG * A * Geo<K>::KP, acc);
 }
 
 // Filter gradient of one DR-row dy block for the filter rows [a_lo, a_lo + nrows):
 // acc[s][b] += sum_{py, px} dy[py][px] * x~[py + a_lo + s][px + b]   (tile-local)
 // `dyb` points at the staged dy of block row 0 (lane column), `xw` at the
 // staged x row (block row 0 + a_lo) at the lane's first column.
-template <int K, int AT, int DYP, int DR>
-__device__ __forceinline__ void dw_block(const float* __restrict__ dyb,
-                                         const float* __restrict__ xw, int nrows,
+template <int K, int AT, int DYP, int DR, typename TS>
+__device__ __forceinline__ void dw_block(const TS* __restrict__ dyb,
+                                         const TS* __restrict__ xw, int nrows,
                                          float (&acc)[AT][K]) {
   using G = Geo<K>;
   float d[DR][4];
 #pragma unroll
   for (int py = 0; py < DR; ++py) {
-    const float4 t = lds128_pinned(dyb + py * DYP);
+    const float4 t = Tile<TS>::load4_pinned(dyb + py * DYP);
     d[py][0] = t.x;
     d[py][1] = t.y;
     d[py][2] = t.z;
@@ -317,7 +347,7 @@ __device__ __forceinline__ void dw_block(const float* __restrict__ dyb,
   for (int ir = 0; ir < DR + AT - 1; ++ir) {
     if (ir >= DR + nrows - 1) break;
     float buf[4 * G::NV];
-    load_window_row<K>(xw + ir * G::SP, buf);
+    load_window_row<K, TS>(xw + ir * G::SP, buf);
 #pragma unroll
     for (int s = 0; s < AT; ++s) {
       const int py = ir - s;
@@ -355,7 +385,7 @@ __global__ void __launch_bounds__(kThreads) dw_fwd_kernel(const T* __restrict__ 
   constexpr int TH = kWarps * PY;
   extern __shared__ __align__(16) float smem[];
   float* sm_w = smem;
-  float* sm_x = smem + G::WPAD;
+  T* sm_x = reinterpret_cast<T*>(smem + G::WPAD);
 
   int64_t t = blockIdx.x;
   const int tx = (int)(t % tiles_x);
@@ -374,7 +404,7 @@ __global__ void __launch_bounds__(kThreads) dw_fwd_kernel(const T* __restrict__ 
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float acc[PY][4];
-  fwd_block<K, PY>(sm_x + warp * PY * G::SP + 4 * lane, sm_w, acc);
+  fwd_block<K, PY, T>(sm_x + warp * PY * G::SP + 4 * lane, sm_w, acc);
   store_block<T, PY>(y + plane_off, H, W, ty0 + warp * PY, tx0 + 4 * lane, vec != 0, acc);
 }
 
@@ -385,7 +415,7 @@ __global__ void __launch_bounds__(kThreads) dw_fwd_kernel(const T* __restrict__ 
 //         a halo).
 // A CTA owns `tpc` consecutive 64 x 128 tiles of one plane and writes one
 // K*K vector of FP32 partial sums to partials[blockIdx.x].
-template <int K, int MODE>
+template <int K, int MODE, typename T>
 struct BwdShape {
   using G = Geo<K>;
   static constexpr int NDX = MODE == 0 ? 4 : 0;
@@ -399,11 +429,12 @@ struct BwdShape {
   static constexpr int DY_HC = MODE == 0 ? G::RP : 0;
   static constexpr int DY_P = MODE == 0 ? G::SP : kTileW;
   static constexpr int DY_ROWS = kBwdTileH + 2 * DY_HR;
+  // byte offsets: staged tiles in the storage type, filter and reduction FP32
   static constexpr int SM_X = 0;
-  static constexpr int SM_DY = X_ROWS * G::SP;
-  static constexpr int SM_W = SM_DY + DY_ROWS * DY_P;
-  static constexpr int SM_RED = SM_W + G::WPAD;
-  static constexpr int SM_FLOATS = SM_RED + NDW * AT * K;
+  static constexpr int SM_DY = X_ROWS * G::SP * (int)sizeof(T);
+  static constexpr int SM_W = SM_DY + DY_ROWS * DY_P * (int)sizeof(T);
+  static constexpr int SM_RED = SM_W + G::WPAD * 4;
+  static constexpr int SM_BYTES = SM_RED + NDW * AT * K * 4;
   static_assert(NDW % GT == 0, "filter-row groups must divide the dw warps");
   static_assert(kBwdTileH % (WPG * 8) == 0, "dw warps own whole 8-row blocks");
   static_assert(16 % bwd_block_rows<K>() == 0, "input-gradient warps own 16 rows");
@@ -413,10 +444,9 @@ __device__ __forceinline__ int group_lo(int g, int K, int GT) { return g * K / G
 
 // CTAs per SM the backward kernel is compiled for: the small-K instances are
 // memory-bound and need fewer registers, so a third CTA adds loads in flight.
-// (BF16 staging keeps more values live, so it stays at two.)
 template <typename T, int K>
 constexpr int bwd_min_ctas() {
-  return (K == 1 || (K <= 5 && sizeof(T) == 4)) ? 3 : 2;
+  return K <= 5 ? 3 : 2;
 }
 
 template <typename T, int K, int MODE>
@@ -426,12 +456,13 @@ __global__ void __launch_bounds__(kThreads, bwd_min_ctas<T, K>())
                   int tiles_x, int tiles_per_plane, int chunks_per_plane, int tpc, int clamp,
                   int vec) {
   using G = Geo<K>;
-  using S = BwdShape<K, MODE>;
+  using S = BwdShape<K, MODE, T>;
   extern __shared__ __align__(16) float smem[];
-  float* sm_x = smem + S::SM_X;
-  float* sm_dy = smem + S::SM_DY;
-  float* sm_w = smem + S::SM_W;
-  float* sm_red = smem + S::SM_RED;
+  char* sm = reinterpret_cast<char*>(smem);
+  T* sm_x = reinterpret_cast<T*>(sm + S::SM_X);
+  T* sm_dy = reinterpret_cast<T*>(sm + S::SM_DY);
+  float* sm_w = reinterpret_cast<float*>(sm + S::SM_W);
+  float* sm_red = reinterpret_cast<float*>(sm + S::SM_RED);
 
   const int64_t plane = blockIdx.x / chunks_per_plane;
   const int chunk = blockIdx.x % chunks_per_plane;
@@ -461,7 +492,7 @@ __global__ void __launch_bounds__(kThreads, bwd_min_ctas<T, K>())
       for (int pass = 0; pass < 16 / BR; ++pass) {
         const int r0 = warp * 16 + pass * BR;
         float acc[BR][4];
-        fwd_block<K, BR>(sm_dy + r0 * S::DY_P + 4 * lane, sm_w, acc);
+        fwd_block<K, BR, T>(sm_dy + r0 * S::DY_P + 4 * lane, sm_w, acc);
         store_block<T, BR>(dx + plane_off, H, W, ty0 + r0, tx0 + 4 * lane, vec != 0, acc);
       }
     }
@@ -490,8 +521,9 @@ __global__ void __launch_bounds__(kThreads, bwd_min_ctas<T, K>())
       constexpr int BR = bwd_block_rows<K>();
 #pragma unroll 1
       for (int r0 = part * S::DW_ROWS; r0 < (part + 1) * S::DW_ROWS; r0 += BR) {
-        dw_block<K, S::AT, S::DY_P, BR>(sm_dy + (r0 + S::DY_HR) * S::DY_P + S::DY_HC + 4 * lane,
-                                        sm_x + (r0 + a_lo) * G::SP + 4 * lane, nrows, acc);
+        dw_block<K, S::AT, S::DY_P, BR, T>(
+            sm_dy + (r0 + S::DY_HR) * S::DY_P + S::DY_HC + 4 * lane,
+            sm_x + (r0 + a_lo) * G::SP + 4 * lane, nrows, acc);
       }
     }
     // warp reduction (fixed butterfly order), one row of sm_red per warp

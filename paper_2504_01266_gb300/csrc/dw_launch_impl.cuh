@@ -11,7 +11,7 @@ template <typename T, int K, int PY>
 static cudaError_t fwd_impl(const DwArgs& a, bool input_grad, cudaStream_t st) {
   using G = Geo<K>;
   constexpr int TH = kWarps * PY;
-  const size_t smem = sizeof(float) * (G::WPAD + (size_t)(TH + 2 * G::R) * G::SP);
+  const size_t smem = sizeof(float) * G::WPAD + sizeof(T) * (size_t)(TH + 2 * G::R) * G::SP;
   auto kern = dw_fwd_kernel<T, K, PY>;
   cudaError_t e = set_smem_once<dw_fwd_kernel<T, K, PY>>(smem);
   if (e != cudaSuccess) return e;
@@ -40,8 +40,8 @@ cudaError_t dw_fwd_launch(const DwArgs& a, const DwConfig& cfg, bool input_grad,
 
 template <typename T, int K, int MODE>
 static cudaError_t bwd_impl(const DwArgs& a, const DwConfig& cfg, cudaStream_t st) {
-  using S = BwdShape<K, MODE>;
-  const size_t smem = sizeof(float) * (size_t)S::SM_FLOATS;
+  using S = BwdShape<K, MODE, T>;
+  const size_t smem = (size_t)S::SM_BYTES;
   auto kern = dw_bwd_kernel<T, K, MODE>;
   cudaError_t e = set_smem_once<dw_bwd_kernel<T, K, MODE>>(smem);
   if (e != cudaSuccess) return e;

@@ -53,7 +53,7 @@ struct RagParams {
   int border;
 };
 
-template <int K>
+template <int K, typename T>
 struct RagShape {
   using G = Geo<K>;
   static constexpr int GT = dw_groups<K>();
@@ -61,34 +61,32 @@ struct RagShape {
   static constexpr int AT = (K + GT - 1) / GT;
   static constexpr int DW_ROWS = kBwdTileH / WPG;
   static constexpr int ROWS = kBwdTileH + 2 * G::R;
+  // byte offsets: staged tiles in the storage type, filters and reduction FP32
   static constexpr int SM_X = 0;
-  static constexpr int SM_DY = ROWS * G::SP;
-  static constexpr int SM_W = 2 * ROWS * G::SP;
-  static constexpr int SM_WF = SM_W + G::WPAD;
-  static constexpr int SM_RED = SM_WF + G::WPAD;
-  static constexpr int SM_FLOATS = SM_RED + 4 * AT * K;
+  static constexpr int SM_DY = ROWS * G::SP * (int)sizeof(T);
+  static constexpr int SM_W = 2 * ROWS * G::SP * (int)sizeof(T);
+  static constexpr int SM_WF = SM_W + G::WPAD * 4;
+  static constexpr int SM_RED = SM_WF + G::WPAD * 4;
+  static constexpr int SM_BYTES = SM_RED + 4 * AT * K * 4;
 };
 
-constexpr int rag_smem_floats(int K) {
-  return K == 1 ? RagShape<1>::SM_FLOATS : K == 3 ? RagShape<3>::SM_FLOATS
-       : K == 5 ? RagShape<5>::SM_FLOATS : K == 7 ? RagShape<7>::SM_FLOATS
-       : K == 9 ? RagShape<9>::SM_FLOATS : K == 11 ? RagShape<11>::SM_FLOATS
-       : K == 13 ? RagShape<13>::SM_FLOATS : RagShape<15>::SM_FLOATS;
+template <typename T>
+constexpr size_t rag_max_smem() {
+  return (size_t)RagShape<15, T>::SM_BYTES;
 }
-
-constexpr size_t kRagMaxSmem = sizeof(float) * (size_t)RagShape<15>::SM_FLOATS;
 
 template <typename T, int K>
 __device__ __forceinline__ void rag_chunk(const RagParams& p, const RagChunk& ch,
                                           const RagImage& im, float* smem, int* s_flag) {
   using G = Geo<K>;
-  using S = RagShape<K>;
+  using S = RagShape<K, T>;
   constexpr int KK = K * K;
-  float* sm_x = smem + S::SM_X;
-  float* sm_dy = smem + S::SM_DY;
-  float* sm_w = smem + S::SM_W;
-  float* sm_wf = smem + S::SM_WF;
-  float* sm_red = smem + S::SM_RED;
+  char* sm = reinterpret_cast<char*>(smem);
+  T* sm_x = reinterpret_cast<T*>(sm + S::SM_X);
+  T* sm_dy = reinterpret_cast<T*>(sm + S::SM_DY);
+  float* sm_w = reinterpret_cast<float*>(sm + S::SM_W);
+  float* sm_wf = reinterpret_cast<float*>(sm + S::SM_WF);
+  float* sm_red = reinterpret_cast<float*>(sm + S::SM_RED);
 
   const int H = im.H, W = im.W;
   const int tiles_x = (W + kTileW - 1) / kTileW;
@@ -111,7 +109,7 @@ __device__ __forceinline__ void rag_chunk(const RagParams& p, const RagChunk& ch
 
   if (role < 2) {
     const bool active = role == 0 ? do_fwd : do_dx;
-    const float* src = role == 0 ? sm_x : sm_dy;
+    const T* src = role == 0 ? sm_x : sm_dy;
     const float* f = role == 0 ? sm_w : sm_wf;
     T* dst = role == 0 ? yp : dxp;
     for (int t = ch.tile_begin; t < ch.tile_end; ++t) {
@@ -130,7 +128,7 @@ __device__ __forceinline__ void rag_chunk(const RagParams& p, const RagChunk& ch
         for (int pass = 0; pass < 16 / BR; ++pass) {
           const int r0 = wl * 16 + pass * BR;
           float acc[BR][4];
-          fwd_block<K, BR>(src + r0 * G::SP + 4 * lane, f, acc);
+          fwd_block<K, BR, T>(src + r0 * G::SP + 4 * lane, f, acc);
           store_block<T, BR>(dst, H, W, ty0 + r0, tx0 + 4 * lane, vec, acc);
         }
       }
@@ -161,8 +159,8 @@ __device__ __forceinline__ void rag_chunk(const RagParams& p, const RagChunk& ch
         constexpr int BR = bwd_block_rows<K>();
 #pragma unroll 1
         for (int r0 = part * S::DW_ROWS; r0 < (part + 1) * S::DW_ROWS; r0 += BR)
-          dw_block<K, S::AT, G::SP, BR>(sm_dy + (r0 + G::R) * G::SP + G::RP + 4 * lane,
-                                        sm_x + (r0 + a_lo) * G::SP + 4 * lane, nrows, acc);
+          dw_block<K, S::AT, G::SP, BR, T>(sm_dy + (r0 + G::R) * G::SP + G::RP + 4 * lane,
+                                           sm_x + (r0 + a_lo) * G::SP + 4 * lane, nrows, acc);
       }
     }
     cta_barrier();
