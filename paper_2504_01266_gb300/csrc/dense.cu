@@ -40,7 +40,7 @@ constexpr int kDenseTileM = 128;     // output pixels per tile
 constexpr int kDenseThreads = 192;
 constexpr int kDenseABytes = kDenseTileM * kDenseC * 2;  // 16 KB
 constexpr int kDenseBBytes = kDenseC * kDenseC * 2;      // 8 KB per tap
-constexpr int kDenseTmemCols = 256;
+constexpr int kDenseTmemCols = 512;
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // give up a wait after 2 s
 
 
@@ -171,6 +171,11 @@ constexpr uint32_t kDenseIdesc = (1u << 4)     // D format F32
                                | ((64u >> 3) << 17)    // N
                                | ((128u >> 4) << 24);  // M
 
+// M = 128, N = n (a multiple of 64 here), both operands K-major.
+__device__ __forceinline__ uint32_t kDenseIdescN(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((128u >> 4) << 24);
+}
+
 // Same shape with both operands MN-major (filter gradient).
 constexpr uint32_t kDenseIdescMN = kDenseIdesc | (1u << 15) | (1u << 16);
 
@@ -203,6 +208,19 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ __forceinline__ void tc_st16_zero(uint32_t taddr) {
+  const uint32_t z = 0;
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, "
+      "%1, %1, %1, %1, %1};" ::"r"(taddr),
+      "r"(z)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_wait_st() {
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
 __device__ __forceinline__ void tc_wait_ld() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
@@ -230,7 +248,7 @@ constexpr int kBandPx = kDenseTileM + 2;              // 130 pixels
 constexpr int kBandBytes = kBandPx * kDenseC * 2;     // 16,640 bytes loaded
 constexpr int kSlotBytes = 17 * 1024;                 // 1024-aligned slot
 constexpr int kBandSlots = 6;
-constexpr int kAccBufs = 4;                            // TMEM accumulators (64 columns each)
+constexpr int kAccBufs = 8;                            // TMEM accumulators (64 columns each)
 constexpr int kOutBufs = 2;                            // output staging tiles (16 KB each)
 constexpr size_t kDenseSmemBand = 1024 + kDenseTaps * kDenseBBytes + kBandSlots * kSlotBytes +
                                   kOutBufs * kDenseABytes + 256;
@@ -293,9 +311,11 @@ __global__ void __launch_bounds__(kDenseThreads, 1)
   if (warp == 0) {
     if (lane == 0) {
       // ---------------------------------------------------------- producer
+      // taps are stored shift-major: slot (b * 3 + a), so the three taps of one
+      // pixel shift b form one 192-row B operand
       mbar_expect_tx(bfull, kDenseTaps * kDenseBBytes);
       for (int t = 0; t < kDenseTaps; ++t)
-        tma_load_2d(sB + t * kDenseBBytes, &tmap_w, t * kDenseC, 0, bfull);
+        tma_load_2d(sB + ((t % 3) * 3 + t / 3) * kDenseBBytes, &tmap_w, t * kDenseC, 0, bfull);
       uint32_t seq = 0;  // global band-load counter: slot seq % S, phase (seq / S) & 1
       for (int64_t tile = t_begin; tile < t_end && !s_abort;) {
         // a run of rows of one strip: [tile, run_end)
@@ -320,61 +340,69 @@ __global__ void __launch_bounds__(kDenseThreads, 1)
   } else if (warp == 1) {
     if (lane == 0) {
       // ------------------------------------------------------- MMA issuer
+      // Band rho (an input row) with pixel shift b feeds output rows rho + 1,
+      // rho, rho - 1 through taps a = 0, 1, 2: one MMA of N = 64 * (number of
+      // those rows inside the run) into their accumulators.  Output row number
+      // o (in CTA order) owns TMEM block acc_block(o) = R - 1 - (o mod R), so
+      // rows o + 1, o, o - 1 sit in ascending blocks (split where the ring
+      // wraps).  Blocks arrive zeroed from the epilogue; every MMA accumulates.
       bool ok = mbar_wait(bfull, 0);
       if (!ok) dense_fail(p.err, &s_abort);
-      uint32_t seq = 0;  // band counter of the first band of the current run
-      int acc = 0;
-      uint32_t acc_phase = 0;
+      uint32_t seq = 0;   // band counter
+      int64_t o_base = 0; // output-row number of the first row of the current run
       const uint32_t b_base = s_addr(sB);
       const uint32_t a_base = s_addr(sA);
+      auto blk = [](int64_t o) { return kAccBufs - 1 - (int)(((o % kAccBufs) + kAccBufs) % kAccBufs); };
       for (int64_t tile = t_begin; ok && tile < t_end && !s_abort;) {
-        const int i0 = (int)(tile % p.H);
         const int64_t strip = tile / p.H;
         const int64_t run_end = min(t_end, (strip + 1) * (int64_t)p.H);
         const int rows = (int)(run_end - tile);
-        // bands of this run: seq .. seq + rows + 1 (rows i0 - 1 .. i0 + rows)
-        for (int k = 0; k < rows && ok; ++k) {
-          // output row i0 + k uses bands seq + k, seq + k + 1, seq + k + 2;
-          // wait for the newest ones (the oldest were waited for earlier)
-          for (int q = (k == 0 ? 0 : 2); q < 3; ++q) {
-            const uint32_t b = seq + k + q;
-            if (!mbar_wait(full + b % kBandSlots, (b / kBandSlots) & 1)) {
+        for (int k = 0; k < rows + 2 && ok; ++k) {
+          // band k of the run is input row i0 - 1 + k; output row (run-local) k - 1
+          const int64_t o_rho = o_base + k - 1;
+          const int a_lo = (k - 1 + 1 <= rows - 1) ? 0 : ((k - 1 <= rows - 1) ? 1 : 2);
+          const int a_hi = (k - 2 >= 0) ? 2 : ((k - 1 >= 0) ? 1 : 0);
+          const uint32_t band = seq + k;
+          if (!mbar_wait(full + band % kBandSlots, (band / kBandSlots) & 1)) {
+            dense_fail(p.err, &s_abort);
+            ok = false;
+            break;
+          }
+          if (a_lo == 0) {
+            // row o_rho + 1 is touched for the first time: its block must be free
+            const int64_t o_new = o_rho + 1;
+            if (!mbar_wait(tempty + blk(o_new), (uint32_t)((o_new / kAccBufs) & 1))) {
               dense_fail(p.err, &s_abort);
               ok = false;
               break;
             }
           }
-          if (!ok) break;
-          if (!mbar_wait(tempty + acc, acc_phase ^ 1)) {
-            dense_fail(p.err, &s_abort);
-            ok = false;
-            break;
-          }
           tc_fence_after();
-          const uint32_t d_tmem = tmem_base + (uint32_t)(acc * 64);
+          const int na = a_hi - a_lo + 1;
+          const int q0 = blk(o_rho + 1 - a_lo);
+          const int n1 = min(na, kAccBufs - q0);  // taps before the ring wraps
+          const uint32_t a_slot = a_base + (band % kBandSlots) * kSlotBytes;
+#pragma unroll 1
+          for (int b = 0; b < 3; ++b) {
+            const uint32_t a_row = a_slot + b * 128;
+            const uint32_t b_row = b_base + (b * 3 + a_lo) * kDenseBBytes;
 #pragma unroll
-          for (int t = 0; t < kDenseTaps; ++t) {
-            const uint32_t band = seq + k + t / 3;
-            const uint32_t a_row = a_base + (band % kBandSlots) * kSlotBytes + (t % 3) * 128;
-#pragma unroll
-            for (int kk = 0; kk < kDenseC / 16; ++kk)
-              tc_mma(d_tmem, sw128_desc(a_row + 32 * kk),
-                     sw128_desc(b_base + t * kDenseBBytes + 32 * kk), kDenseIdesc,
-                     (t > 0 || kk > 0) ? 1u : 0u);
+            for (int kk = 0; kk < kDenseC / 16; ++kk) {
+              tc_mma(tmem_base + (uint32_t)(q0 * 64), sw128_desc(a_row + 32 * kk),
+                     sw128_desc(b_row + 32 * kk),
+                     kDenseIdescN(64 * n1), 1u);
+              if (n1 < na)
+                tc_mma(tmem_base, sw128_desc(a_row + 32 * kk),
+                       sw128_desc(b_row + n1 * kDenseBBytes + 32 * kk),
+                       kDenseIdescN(64 * (na - n1)), 1u);
+            }
           }
-          // the band of row i0 + k - 1 is not read again in this run
-          tc_commit(empty + (seq + k) % kBandSlots);
-          tc_commit(tfull + acc);
-          if (++acc == kAccBufs) {
-            acc = 0;
-            acc_phase ^= 1;
-          }
+          tc_commit(empty + band % kBandSlots);
+          if (a_hi == 2) tc_commit(tfull + blk(o_rho - 1));  // row o_rho - 1 is complete
         }
         if (!ok) break;
-        // release the run's last two bands
-        tc_commit(empty + (seq + rows) % kBandSlots);
-        tc_commit(empty + (seq + rows + 1) % kBandSlots);
         seq += rows + 2;
+        o_base += rows;
         tile = run_end;
       }
     }
@@ -385,13 +413,22 @@ __global__ void __launch_bounds__(kDenseThreads, 1)
     const int quad = warp & 3;  // TMEM lane quadrant this warp may access
     const int row = quad * 32 + lane;
     const bool leader = (warp == 2 && lane == 0);
-    int acc = 0, ob = 0;
-    uint32_t acc_phase = 0;
-    for (int64_t tile = t_begin; tile < t_end; ++tile) {
+    const uint32_t lane_base = tmem_base + ((uint32_t)(quad * 32) << 16);
+    // every accumulator block starts zeroed (phase 0 of its "free" barrier)
+    for (int q = 0; q < kAccBufs; ++q)
+      for (int c = 0; c < 4; ++c) tc_st16_zero(lane_base + (uint32_t)(q * 64 + 16 * c));
+    tc_wait_st();
+    tc_fence_before();
+    for (int q = 0; q < kAccBufs; ++q) mbar_arrive(tempty + q);
+    int ob = 0;
+    int64_t o = 0;  // output-row number in CTA order
+    for (int64_t tile = t_begin; tile < t_end; ++tile, ++o) {
+      const int q = kAccBufs - 1 - (int)(o % kAccBufs);
+      const uint32_t par = (uint32_t)((o / kAccBufs) & 1);
       // The leader alone does the bounded waits and broadcasts the outcome, so
       // the four warps leave the loop together (they share a named barrier).
       if (leader) {
-        int ok = !s_abort && mbar_wait(tfull + acc, acc_phase);
+        int ok = !s_abort && mbar_wait(tfull + q, par);
         if (!ok) dense_fail(p.err, &s_abort);
         // staging buffer ob is free once the store issued from it two tiles
         // ago has finished reading it
@@ -401,32 +438,36 @@ __global__ void __launch_bounds__(kDenseThreads, 1)
       epilogue_barrier();
       if (!s_go) break;
       tc_fence_after();
-      const uint32_t taddr = tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(acc * 64);
+      const uint32_t taddr = lane_base + (uint32_t)(q * 64);
       float v[64];
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
         float part[16];
         tc_ld16(taddr + 16 * c, part);
 #pragma unroll
-        for (int q = 0; q < 16; ++q) v[16 * c + q] = part[q];
+        for (int z = 0; z < 16; ++z) v[16 * c + z] = part[z];
       }
       tc_wait_ld();
+      // hand the block back zeroed for the row o + R
+#pragma unroll
+      for (int c = 0; c < 4; ++c) tc_st16_zero(taddr + 16 * c);
+      tc_wait_st();
       tc_fence_before();
-      mbar_arrive(tempty + acc);
+      mbar_arrive(tempty + q);
       uint8_t* out_row = sOut + ob * kDenseABytes + row * 128;
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
+      for (int z = 0; z < 8; ++z) {
         uint4 u;
-        __nv_bfloat162 h0 = __floats2bfloat162_rn(v[8 * q + 0], v[8 * q + 1]);
-        __nv_bfloat162 h1 = __floats2bfloat162_rn(v[8 * q + 2], v[8 * q + 3]);
-        __nv_bfloat162 h2 = __floats2bfloat162_rn(v[8 * q + 4], v[8 * q + 5]);
-        __nv_bfloat162 h3 = __floats2bfloat162_rn(v[8 * q + 6], v[8 * q + 7]);
+        __nv_bfloat162 h0 = __floats2bfloat162_rn(v[8 * z + 0], v[8 * z + 1]);
+        __nv_bfloat162 h1 = __floats2bfloat162_rn(v[8 * z + 2], v[8 * z + 3]);
+        __nv_bfloat162 h2 = __floats2bfloat162_rn(v[8 * z + 4], v[8 * z + 5]);
+        __nv_bfloat162 h3 = __floats2bfloat162_rn(v[8 * z + 6], v[8 * z + 7]);
         u.x = *reinterpret_cast<uint32_t*>(&h0);
         u.y = *reinterpret_cast<uint32_t*>(&h1);
         u.z = *reinterpret_cast<uint32_t*>(&h2);
         u.w = *reinterpret_cast<uint32_t*>(&h3);
-        // 128-byte swizzle: 16-byte chunk q of row r lives at chunk q ^ (r % 8)
-        *reinterpret_cast<uint4*>(out_row + ((q ^ (row & 7)) << 4)) = u;
+        // 128-byte swizzle: 16-byte chunk z of row r lives at chunk z ^ (r % 8)
+        *reinterpret_cast<uint4*>(out_row + ((z ^ (row & 7)) << 4)) = u;
       }
       fence_proxy_async();
       epilogue_barrier();
@@ -439,10 +480,6 @@ __global__ void __launch_bounds__(kDenseThreads, 1)
         bulk_commit();
       }
       ob ^= 1;
-      if (++acc == kAccBufs) {
-        acc = 0;
-        acc_phase ^= 1;
-      }
     }
     if (leader) bulk_wait_all();
   }
