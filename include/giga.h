@@ -175,7 +175,11 @@ giga_status_t giga_conv2d_batched_workspace_size(const giga_image_t* images, int
                                                  int32_t ops, size_t* bytes);
 
 /* ------------------------------------------------------------------------
- * Autotuner.  Candidates: tile height / rows per thread / tiles per CTA.
+ * Autotuner.  Candidates: forward and input gradient (op 1 / 2): id 0..3 =
+ * {8, 4} rows per thread (bit 0) x {one tile per CTA, persistent
+ * double-buffered CTAs} (bit 1); filter gradient and the fused backward
+ * (op 4 / 6): id 0..4 = tiles per CTA {auto, 2, 4, 8, 16}.  The built-in
+ * default is id 0.
  * Modes (also from the environment variable GIGA_AUTOTUNE=off|cached|full):
  *   0 off:    always the built-in default configuration;
  *   1 cached: use a cached choice when one exists (default);
@@ -191,7 +195,8 @@ int32_t giga_autotune_get_mode(void);
 giga_status_t giga_autotune_conv2d(const giga_conv2d_desc_t* desc, int32_t ops, const void* x,
                                    const void* w, void* y, const void* dy, void* dx, float* dw,
                                    void* ws, size_t ws_bytes, void* stream);
-/* The configuration id the entry points will use for (desc, op); -1 on error. */
+/* The configuration id the entry points will use for (desc, op): the cached
+ * choice, else 0; -1 on error. */
 int32_t giga_autotune_choice(const giga_conv2d_desc_t* desc, int32_t op);
 giga_status_t giga_autotune_save(const char* path);
 giga_status_t giga_autotune_load(const char* path);

@@ -44,7 +44,10 @@ int tune_mode() {
   return g_mode;
 }
 
-int tune_candidates(int op) { return (op == TUNE_FWD || op == TUNE_BWD_INPUT) ? 2 : 5; }
+// Forward / input gradient: {8, 4} rows per thread x {one tile per CTA,
+// persistent}; filter gradient: tiles per CTA {auto, 2, 4, 8, 16}.
+int tune_candidates(int op) { return (op == TUNE_FWD || op == TUNE_BWD_INPUT) ? 4 : 5; }
+
 
 static int auto_tiles_per_cta(const DwArgs& a) {
   const int64_t tiles = a.N * a.C * (int64_t)((a.W + kTileW - 1) / kTileW) *
@@ -58,9 +61,11 @@ static int auto_tiles_per_cta(const DwArgs& a) {
 DwConfig tune_config(int op, int id, const DwArgs& a) {
   DwConfig c;
   c.rows_per_thread = 8;
+  c.persistent = 0;
   c.tiles_per_cta = auto_tiles_per_cta(a);
   if (op == TUNE_FWD || op == TUNE_BWD_INPUT) {
-    c.rows_per_thread = id == 1 ? 4 : 8;
+    c.rows_per_thread = (id & 1) ? 4 : 8;
+    c.persistent = (id & 2) ? 1 : 0;
   } else {
     static const int tpc[5] = {0, 2, 4, 8, 16};
     if (id >= 1 && id <= 4) c.tiles_per_cta = tpc[id];

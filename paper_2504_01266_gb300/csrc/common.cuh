@@ -36,6 +36,7 @@ struct DwArgs {
 // Launch configuration chosen by the autotuner (or the defaults).
 struct DwConfig {
   int rows_per_thread;  // forward / input-gradient kernel: 4 or 8
+  int persistent;       // forward / input-gradient kernel: 1 = persistent, double-buffered
   int tiles_per_cta;    // filter-gradient kernels: consecutive tiles per CTA
 };
 
@@ -79,6 +80,9 @@ template <> struct Elem<__nv_bfloat16> {
 
 // Host-side launch accounting (giga_launch_count).
 void note_launch(int n = 1);
+
+// Multiprocessors of the current device (cached per device).
+int sm_count();
 
 // Raise a kernel's dynamic shared-memory limit once per device (the attribute
 // is per context; later calls are a bit test).  One flag word per kernel.

@@ -83,6 +83,11 @@ __device__ __forceinline__ void cp_async8(void* dst, const void* src, bool valid
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 // Wait for this thread's staging copies, then for the whole CTA.
 __device__ __forceinline__ void stage_wait() {
   cp_async_wait_all();
@@ -226,6 +231,20 @@ __device__ __forceinline__ void stage_tile(T* __restrict__ sm, const T* __restri
     }
   }
   cp_async_commit();
+}
+
+// Stage a K x K filter asynchronously (4-byte cp.async; padding columns are
+// zero-filled by the same copies), optionally rotated by 180 degrees.
+template <int K>
+__device__ __forceinline__ void stage_filter_async(float* __restrict__ sm,
+                                                   const float* __restrict__ w, bool flip,
+                                                   int NT) {
+  constexpr int KP = Geo<K>::KP;
+  for (int k = threadIdx.x; k < K * KP; k += NT) {
+    const int a = k / KP, b = k - (k / KP) * KP;
+    const bool ok = b < K;
+    cp_async4(sm + k, ok ? w + (flip ? (K - 1 - a) * K + (K - 1 - b) : a * K + b) : w, ok);
+  }
 }
 
 // Stage a K x K filter with rows padded to KP (zeros), optionally rotated by
@@ -372,40 +391,71 @@ constexpr int bwd_block_rows() {
 }
 
 // ---------------------------------------------------------------- forward
-// One CTA per output tile of (kWarps * PY) x 128 pixels.  With flip = 1 the
-// staged filter is rotated by 180 degrees: that computes g (input gradient,
-// zero border) from dy.
+// Persistent: CTA b handles tiles b, b + G, b + 2G, ... (G = gridDim.x, so
+// neighbouring CTAs work on neighbouring tiles at the same time and share
+// halos in L2), each (kWarps * PY) x 128 pixels of one plane.  Two stages of
+// shared memory: while a tile is computed, the cp.async copies of the next
+// tile and of its plane's filter are in flight.  With flip = 1 the filter is
+// rotated by 180 degrees: that computes g (input gradient, zero border) from dy.
+template <int K, int PY, typename T>
+struct FwdShape {
+  using G = Geo<K>;
+  static constexpr int TH = kWarps * PY;
+  static constexpr int TILE_BYTES = (TH + 2 * G::R) * G::SP * (int)sizeof(T);
+  static constexpr int STAGE_BYTES = G::WPAD * 4 + TILE_BYTES;  // filter, then tile
+  static constexpr int SM_BYTES = 2 * STAGE_BYTES;
+};
+
 template <typename T, int K, int PY>
 __global__ void __launch_bounds__(kThreads) dw_fwd_kernel(const T* __restrict__ x,
                                                           const float* __restrict__ w,
                                                           T* __restrict__ y, int C, int H, int W,
-                                                          int tiles_x, int tiles_y, int clamp,
-                                                          int vec, int flip) {
+                                                          int tiles_x, int tiles_y,
+                                                          int64_t num_tiles, int clamp, int vec,
+                                                          int flip) {
   using G = Geo<K>;
-  constexpr int TH = kWarps * PY;
+  using S = FwdShape<K, PY, T>;
+  constexpr int TH = S::TH;
   extern __shared__ __align__(16) float smem[];
-  float* sm_w = smem;
-  T* sm_x = reinterpret_cast<T*>(smem + G::WPAD);
+  char* sm = reinterpret_cast<char*>(smem);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  auto stage = [&](int64_t t, int sb) {
+    const int tx = (int)(t % tiles_x);
+    const int64_t t2 = t / tiles_x;
+    const int ty = (int)(t2 % tiles_y);
+    const int64_t plane = t2 / tiles_y;
+    float* sw = reinterpret_cast<float*>(sm + sb * S::STAGE_BYTES);
+    T* sx = reinterpret_cast<T*>(sm + sb * S::STAGE_BYTES + G::WPAD * 4);
+    stage_filter_async<K>(sw, w + (int64_t)(plane % C) * K * K, flip != 0, kThreads);
+    stage_tile<T, G::R, G::RP, G::SP>(sx, x + plane * (int64_t)H * W, H, W, ty * TH,
+                                      tx * kTileW, TH + 2 * G::R, clamp != 0, vec != 0);
+  };
 
   int64_t t = blockIdx.x;
-  const int tx = (int)(t % tiles_x);
-  t /= tiles_x;
-  const int ty = (int)(t % tiles_y);
-  const int64_t plane = t / tiles_y;
-  const int c = (int)(plane % C);
-
-  stage_filter<K>(sm_w, w + (int64_t)c * K * K, flip != 0, kThreads);
-
-  const int ty0 = ty * TH, tx0 = tx * kTileW;
-  const int64_t plane_off = plane * (int64_t)H * W;
-  stage_tile<T, G::R, G::RP, G::SP>(sm_x, x + plane_off, H, W, ty0, tx0, TH + 2 * G::R,
-                                    clamp != 0, vec != 0);
-  stage_wait();
-
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float acc[PY][4];
-  fwd_block<K, PY, T>(sm_x + warp * PY * G::SP + 4 * lane, sm_w, acc);
-  store_block<T, PY>(y + plane_off, H, W, ty0 + warp * PY, tx0 + 4 * lane, vec != 0, acc);
+  if (t >= num_tiles) return;
+  stage(t, 0);
+  for (int sb = 0; t < num_tiles; t += gridDim.x, sb ^= 1) {
+    const int64_t tn = t + gridDim.x;
+    if (tn < num_tiles) {
+      stage(tn, sb ^ 1);  // the other stage was released by the barrier below
+      cp_async_wait_group<1>();
+    } else {
+      cp_async_wait_group<0>();
+    }
+    cta_barrier();
+    const int tx = (int)(t % tiles_x);
+    const int64_t t2 = t / tiles_x;
+    const int ty = (int)(t2 % tiles_y);
+    const int64_t plane = t2 / tiles_y;
+    const float* sw = reinterpret_cast<const float*>(sm + sb * S::STAGE_BYTES);
+    const T* sx = reinterpret_cast<const T*>(sm + sb * S::STAGE_BYTES + G::WPAD * 4);
+    float acc[PY][4];
+    fwd_block<K, PY, T>(sx + warp * PY * G::SP + 4 * lane, sw, acc);
+    store_block<T, PY>(y + plane * (int64_t)H * W, H, W, ty * TH + warp * PY,
+                       tx * kTileW + 4 * lane, vec != 0, acc);
+    cta_barrier();  // every warp is done with stage sb before it is refilled
+  }
 }
 
 // -------------------------------------------------------------- backward

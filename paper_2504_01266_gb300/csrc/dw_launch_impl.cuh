@@ -2,26 +2,49 @@
 // only by the per-filter-size translation units dw_kNN.cu.
 #pragma once
 
+#include <algorithm>
+
 #include "dw_kernels.cuh"
 #include "dw_launch.h"
 
 namespace giga {
 
+// persistent = 0 (the default, fastest on the measured workloads): one tile
+// per CTA and a single shared-memory stage (the kernel's prefetch branch never
+// runs because gridDim.x >= tiles); 1: as many CTAs as fit on the GPU, each
+// with two stages -- an autotuning candidate.
 template <typename T, int K, int PY>
-static cudaError_t fwd_impl(const DwArgs& a, bool input_grad, cudaStream_t st) {
-  using G = Geo<K>;
-  constexpr int TH = kWarps * PY;
-  const size_t smem = sizeof(float) * G::WPAD + sizeof(T) * (size_t)(TH + 2 * G::R) * G::SP;
+static cudaError_t fwd_impl(const DwArgs& a, bool input_grad, bool persistent, cudaStream_t st) {
+  using S = FwdShape<K, PY, T>;
   auto kern = dw_fwd_kernel<T, K, PY>;
-  cudaError_t e = set_smem_once<dw_fwd_kernel<T, K, PY>>(smem);
+  cudaError_t e = set_smem_once<dw_fwd_kernel<T, K, PY>>((size_t)S::SM_BYTES);
   if (e != cudaSuccess) return e;
   const int64_t tiles_x = (a.W + kTileW - 1) / kTileW;
-  const int64_t tiles_y = (a.H + TH - 1) / TH;
-  const int64_t grid = a.N * a.C * tiles_x * tiles_y;
+  const int64_t tiles_y = (a.H + S::TH - 1) / S::TH;
+  const int64_t tiles = a.N * a.C * tiles_x * tiles_y;
+  int64_t grid = tiles;
+  size_t smem = (size_t)S::STAGE_BYTES;
+  if (persistent) {
+    smem = (size_t)S::SM_BYTES;
+    static int ctas_per_sm[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int& per_sm = ctas_per_sm[dev & 63];
+    if (per_sm == 0) {
+      int v = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kern, kThreads, smem) !=
+              cudaSuccess ||
+          v < 1)
+        v = 1;
+      per_sm = v;
+    }
+    grid = std::min<int64_t>(tiles, (int64_t)per_sm * sm_count());
+  }
+  if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
   const T* in = static_cast<const T*>(input_grad ? a.dy : a.x);
   T* out = static_cast<T*>(input_grad ? a.dx : a.y);
   kern<<<(unsigned)grid, kThreads, smem, st>>>(in, a.w, out, (int)a.C, (int)a.H, (int)a.W,
-                                               (int)tiles_x, (int)tiles_y,
+                                               (int)tiles_x, (int)tiles_y, tiles,
                                                input_grad ? 0 : a.border, a.vec,
                                                input_grad ? 1 : 0);
   note_launch();
@@ -32,10 +55,12 @@ template <int K>
 cudaError_t dw_fwd_launch(const DwArgs& a, const DwConfig& cfg, bool input_grad,
                           cudaStream_t st) {
   const bool py4 = cfg.rows_per_thread == 4;
+  const bool pers = cfg.persistent != 0;
   if (a.dtype == 0)
-    return py4 ? fwd_impl<float, K, 4>(a, input_grad, st) : fwd_impl<float, K, 8>(a, input_grad, st);
-  return py4 ? fwd_impl<__nv_bfloat16, K, 4>(a, input_grad, st)
-             : fwd_impl<__nv_bfloat16, K, 8>(a, input_grad, st);
+    return py4 ? fwd_impl<float, K, 4>(a, input_grad, pers, st)
+               : fwd_impl<float, K, 8>(a, input_grad, pers, st);
+  return py4 ? fwd_impl<__nv_bfloat16, K, 4>(a, input_grad, pers, st)
+             : fwd_impl<__nv_bfloat16, K, 8>(a, input_grad, pers, st);
 }
 
 template <typename T, int K, int MODE>

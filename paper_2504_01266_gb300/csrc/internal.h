@@ -15,8 +15,6 @@ giga_status_t fail(giga_status_t status, const std::string& detail);
 giga_status_t cuda_fail(cudaError_t e, const char* where);
 void clear_error();
 
-int sm_count();  // multiprocessors of the current device (cached per device)
-
 // Autotuner (autotune.cu).
 enum TuneOp { TUNE_FWD = 0, TUNE_BWD_INPUT = 1, TUNE_BWD_FILTER = 2, TUNE_BWD_FUSED = 3 };
 int tune_mode();

@@ -5,6 +5,9 @@ Small cases span several tiles and ragged tails (H, W not multiples of the
 full-size workloads are checked on sampled outputs and on every kind of
 border pixel.  Outputs are poisoned with NaN first, so unwritten elements fail.
 """
+import json
+import math
+
 import numpy as np
 import pytest
 import torch
@@ -134,6 +137,65 @@ def test_misaligned_view_uses_scalar_path(giga):
     xv = base[1:].view(1, 1, 40, 129)
     y = giga.conv2d_fwd(xv, w.cuda(), "clamp")
     assert normwise(to_np(y), oracle.dw_fwd(x.numpy(), w.numpy(), oracle.CLAMP)) <= FP32_TOL
+
+
+def _force_fwd_candidate(tmp_path, shape, K, border, dtype, cand):
+    """Pin the forward and input-gradient configuration through the autotune
+    cache (key: op, dtype, K, border, floor(log2(numel)))."""
+    from paper_2504_01266_gb300 import _lib
+    N, C, H, W = shape
+    dt = _lib.GIGA_F32 if dtype == torch.float32 else _lib.GIGA_BF16
+    b = BORDER[border]
+    sc = int(math.floor(math.log2(N * C * H * W)))
+    path = tmp_path / f"tune_{cand}.json"
+    path.write_text(json.dumps({"giga_autotune": 1, "entries": {
+        f"{op}:{dt}:{K}:{b}:{sc}": cand for op in (0, 1)}}))
+    _lib.giga_autotune_clear()
+    assert _lib.giga_autotune_load(str(path)) == _lib.GIGA_OK
+    d = _lib.desc(N, C, C, H, W, K, C, b, dt, _lib.GIGA_LAYOUT_NCHW)
+    assert _lib.giga_autotune_choice(d, _lib.GIGA_OP_FWD) == cand
+    assert _lib.giga_autotune_choice(d, _lib.GIGA_OP_BWD_INPUT) == cand
+
+
+@pytest.mark.parametrize("K,border,dtype", [
+    (3, "zero", torch.float32), (3, "clamp", torch.float32), (15, "zero", torch.float32),
+    (15, "clamp", torch.float32), (3, "zero", torch.bfloat16), (15, "clamp", torch.bfloat16)])
+def test_fwd_every_configuration(giga, tmp_path, K, border, dtype):
+    """Every forward / input-gradient configuration ({8, 4} rows per thread x
+    one tile per CTA or persistent double-buffered CTAs) on planes holding
+    more tiles than a persistent grid has CTAs, so each persistent CTA runs
+    two or three tiles through its two shared-memory stages and the last
+    round is ragged; W = 998 also takes the scalar staging path."""
+    from paper_2504_01266_gb300 import _lib
+    shape = (4, 4, 520, 998 if dtype == torch.float32 else 1000)
+    x, w, dy = make(shape, K, 600 + K, dtype)
+    xc, wc, dyc = x.cuda(), w.cuda(), dy.cuda()
+    b = BORDER[border]
+    xr, dyr, wn = x.double().numpy(), dy.double().numpy(), w.numpy()
+    ref_y, ref_dx = oracle.dw_fwd(xr, wn, b), oracle.dw_bwd_input(dyr, wn, b)
+    if dtype == torch.float32:
+        mag_y = oracle.dw_fwd(np.abs(xr), np.abs(wn), b)
+        mag_dx = oracle.dw_bwd_input(np.abs(dyr), np.abs(wn), b)
+    mode = _lib.giga_autotune_get_mode()
+    _lib.giga_autotune_set_mode(1)
+    try:
+        for cand in range(4):
+            _force_fwd_candidate(tmp_path, shape, K, border, dtype, cand)
+            y = poison_like(xc)
+            giga.conv2d_fwd(xc, wc, border, out=y)
+            dx = poison_like(dyc)
+            giga.conv2d_bwd_input(dyc, wc, border, out=dx)
+            what = (K, border, dtype, cand)
+            if dtype == torch.float32:
+                assert_fp32(to_np(y), ref_y, mag_y, K * K, what)
+                assert_fp32(to_np(dx), ref_dx, mag_dx, (K // 2 + 1) ** 2 * K * K, what)
+            else:
+                assert not torch.isnan(y).any() and not torch.isnan(dx).any(), what
+                assert normwise(to_np(y), ref_y) <= BF16_KERNEL_TOL, what
+                assert normwise(to_np(dx), ref_dx) <= BF16_KERNEL_TOL, what
+    finally:
+        _lib.giga_autotune_clear()
+        _lib.giga_autotune_set_mode(mode)
 
 
 # ------------------------------------------------------- full-size workloads
