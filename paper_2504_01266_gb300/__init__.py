@@ -109,7 +109,9 @@ def conv2d_bwd_filter(x: torch.Tensor, dy: torch.Tensor, K: int, border="zero", 
 
 def conv2d_bwd(x: torch.Tensor, dy: torch.Tensor, w: torch.Tensor, border="zero",
                dx=None, dw=None, ws=None):
-    """Fused (dx, dw) in one pass over x and dy."""
+    """Both gradients (dx, dw): one fused pass over x and dy, or -- when the
+    autotuner chose it for this problem class -- an input-gradient pass and a
+    filter-gradient pass."""
     _require_cuda(x, dy, w)
     K = w.shape[-1]
     d = dw_desc(x, K, border)

@@ -218,10 +218,23 @@ giga_status_t run_dw_op(int op, const DwArgs& a, const DwConfig& cfg, cudaStream
       if (e != cudaSuccess) return cuda_fail(e, "input-gradient launch");
       return GIGA_OK;
     case TUNE_BWD_FILTER:
+      e = dispatch_k_filter(a.K, [&](auto k) { return dw_filter_launch<decltype(k)::value>(a, cfg, st); });
+      if (e == cudaSuccess)
+        e = dw_finalize_launch(a, dw_bwd_chunks_per_plane(a.H, a.W, cfg.tiles_per_cta), st);
+      if (e != cudaSuccess) return cuda_fail(e, "filter-gradient launch");
+      return GIGA_OK;
     case TUNE_BWD_FUSED: {
-      const int mode = op == TUNE_BWD_FUSED ? 0 : 1;
-      e = dispatch_k_filter(a.K, [&](auto k) { return dw_bwd_launch<decltype(k)::value>(a, cfg, mode, st); });
-      if (e == cudaSuccess && mode == 0) e = dw_fixup_launch(a, st);
+      if (cfg.split) {
+        // input gradient by the forward-style kernel, filter gradient by the
+        // persistent filter kernel: two passes over dy, each role on its own
+        // best kernel (faster for the ALU-bound large filters)
+        DwConfig fc = tune_config(TUNE_FWD, 0, a);
+        giga_status_t s2 = run_dw_op(TUNE_BWD_INPUT, a, fc, st);
+        if (s2 != GIGA_OK) return s2;
+        return run_dw_op(TUNE_BWD_FILTER, a, cfg, st);
+      }
+      e = dispatch_k_filter(a.K, [&](auto k) { return dw_bwd_launch<decltype(k)::value>(a, cfg, st); });
+      if (e == cudaSuccess) e = dw_fixup_launch(a, st);
       if (e == cudaSuccess)
         e = dw_finalize_launch(a, dw_bwd_chunks_per_plane(a.H, a.W, cfg.tiles_per_cta), st);
       if (e != cudaSuccess) return cuda_fail(e, "backward launch");
@@ -455,11 +468,14 @@ const char* giga_last_error_detail(void) { return t_error.c_str(); }
 
 giga_status_t giga_check_device_error(void* stream) {
   clear_error();
-  int code = 0;
+  int code = 0, dw_code = 0;
   cudaError_t e = dense_take_error(static_cast<cudaStream_t>(stream), &code);
+  if (e == cudaSuccess) e = dw_take_error(static_cast<cudaStream_t>(stream), &dw_code);
   if (e != cudaSuccess) return cuda_fail(e, "reading the device error word");
   if (code != 0)
     return fail(GIGA_ERR_TIMEOUT, "a tensor-core kernel gave up waiting on a pipeline barrier");
+  if (dw_code != 0)
+    return fail(GIGA_ERR_TIMEOUT, "a depthwise kernel gave up waiting for a TMA tile copy");
   return GIGA_OK;
 }
 

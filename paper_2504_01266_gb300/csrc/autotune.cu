@@ -45,8 +45,17 @@ int tune_mode() {
 }
 
 // Forward / input gradient: {8, 4} rows per thread x {one tile per CTA,
-// persistent}; filter gradient: tiles per CTA {auto, 2, 4, 8, 16}.
-int tune_candidates(int op) { return (op == TUNE_FWD || op == TUNE_BWD_INPUT) ? 4 : 5; }
+// persistent}; filter gradient: tiles per chunk {auto, 2, 4, 8, 16}; fused
+// backward: the fused kernel with tiles per CTA {auto, 2, 4, 8, 16}, or the
+// two-pass split.
+int tune_candidates(int op) {
+  switch (op) {
+    case TUNE_FWD:
+    case TUNE_BWD_INPUT: return 4;
+    case TUNE_BWD_FILTER: return 5;
+    default: return 6;
+  }
+}
 
 
 static int auto_tiles_per_cta(const DwArgs& a) {
@@ -58,17 +67,50 @@ static int auto_tiles_per_cta(const DwArgs& a) {
   return (int)t;
 }
 
+// The persistent filter kernel runs one CTA per SM over chunks dealt round
+// robin; a chunk ends with a reduction of the accumulators costing about a
+// fifth of a tile.  Pick the chunk length (<= 16 tiles) minimising the
+// busiest CTA's rounds x (tiles + 0.2).
+static int auto_filter_tiles_per_chunk(const DwArgs& a) {
+  const int64_t tpp = (int64_t)((a.W + kTileW - 1) / kTileW) * (int64_t)((a.H + 63) / 64);
+  const int64_t planes = a.N * a.C;
+  const int64_t G = sm_count();
+  int best = 1;
+  double best_cost = 1e300;
+  for (int tpc = 16; tpc >= 1; tpc /= 2) {
+    const int64_t chunks = planes * ((tpp + tpc - 1) / tpc);
+    const double cost = (double)((chunks + G - 1) / G) * (tpc + 0.2);
+    if (cost < best_cost * 0.999) {
+      best_cost = cost;
+      best = tpc;
+    }
+  }
+  return best;
+}
+
 DwConfig tune_config(int op, int id, const DwArgs& a) {
   DwConfig c;
   c.rows_per_thread = 8;
   c.persistent = 0;
-  c.tiles_per_cta = auto_tiles_per_cta(a);
-  if (op == TUNE_FWD || op == TUNE_BWD_INPUT) {
-    c.rows_per_thread = (id & 1) ? 4 : 8;
-    c.persistent = (id & 2) ? 1 : 0;
-  } else {
-    static const int tpc[5] = {0, 2, 4, 8, 16};
-    if (id >= 1 && id <= 4) c.tiles_per_cta = tpc[id];
+  c.split = 0;
+  c.tiles_per_cta = op == TUNE_BWD_FILTER ? auto_filter_tiles_per_chunk(a) : auto_tiles_per_cta(a);
+  static const int tpc[5] = {0, 2, 4, 8, 16};
+  switch (op) {
+    case TUNE_FWD:
+    case TUNE_BWD_INPUT:
+      c.rows_per_thread = (id & 1) ? 4 : 8;
+      c.persistent = (id & 2) ? 1 : 0;
+      break;
+    case TUNE_BWD_FILTER:
+      if (id >= 1 && id <= 4) c.tiles_per_cta = tpc[id];
+      break;
+    default:
+      if (id >= 1 && id <= 4) c.tiles_per_cta = tpc[id];
+      if (id == 5) {
+        c.split = 1;
+        c.tiles_per_cta = auto_filter_tiles_per_chunk(a);
+      }
+      break;
   }
   return c;
 }

@@ -37,7 +37,8 @@ struct DwArgs {
 struct DwConfig {
   int rows_per_thread;  // forward / input-gradient kernel: 4 or 8
   int persistent;       // forward / input-gradient kernel: 1 = persistent, double-buffered
-  int tiles_per_cta;    // filter-gradient kernels: consecutive tiles per CTA
+  int tiles_per_cta;    // filter-gradient kernels: consecutive tiles per chunk
+  int split;            // fused backward: 1 = input and filter gradients as two passes
 };
 
 // Element access for the two storage types; arithmetic is always FP32.

@@ -30,6 +30,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "tma.cuh"
 
 namespace giga {
 
@@ -180,7 +181,7 @@ __device__ __forceinline__ float4 load_chunk(const T* __restrict__ plane, int H,
 // BF16); rows outside a zero border are zero-filled by cp.async; the rest
 // (edges, clamped columns, unaligned rows) go element by element (FP32:
 // 4-byte cp.async; BF16: a plain load and store).  Completion: stage_wait().
-template <typename T, int HR, int HC, int PITCH, int NT = kThreads>
+template <typename T, int HR, int HC, int PITCH, int NT = kThreads, bool COMMIT = true>
 __device__ __forceinline__ void stage_tile(T* __restrict__ sm, const T* __restrict__ plane,
                                            int H, int W, int ty0, int tx0, int rows,
                                            bool clamp, bool vec) {
@@ -230,7 +231,44 @@ __device__ __forceinline__ void stage_tile(T* __restrict__ sm, const T* __restri
       }
     }
   }
-  cp_async_commit();
+  if (COMMIT) cp_async_commit();
+}
+
+// Clamp border on a tile that TMA staged with zeros outside the image: tile
+// row sr is image row ty0 - HR + sr, tile column sc image column tx0 - HC + sc.
+// Pass 1 gives the out-of-image columns of every in-image row the value of
+// the nearest in-image column; pass 2 copies whole rows (corners included)
+// from the nearest in-image row.  Every thread of the CTA calls it; it ends
+// with a barrier.
+template <typename T, int PITCH, int NT>
+__device__ __forceinline__ void clamp_fix(T* __restrict__ sm, int H, int W, int ty0, int tx0,
+                                          int HR, int HC, int rows) {
+  const int c_lo = max(0, HC - tx0), c_hi = min(PITCH, W - tx0 + HC);
+  const int r_lo = max(0, HR - ty0), r_hi = min(rows, H - ty0 + HR);
+  const int nl = c_lo, nr = PITCH - c_hi, ncol = nl + nr;
+  if (ncol > 0) {
+    const int total = (r_hi - r_lo) * ncol;
+    for (int k = threadIdx.x; k < total; k += NT) {
+      const int r = r_lo + k / ncol, c = k - (k / ncol) * ncol;
+      T* row = sm + r * PITCH;
+      if (c < nl)
+        row[c] = row[c_lo];
+      else
+        row[c_hi + (c - nl)] = row[c_hi - 1];
+    }
+    cta_barrier();
+  }
+  const int nt = r_lo, nb = rows - r_hi;
+  if (nt + nb > 0) {
+    const int total = (nt + nb) * PITCH;
+    for (int k = threadIdx.x; k < total; k += NT) {
+      const int r = k / PITCH, c = k - (k / PITCH) * PITCH;
+      const int dst = r < nt ? r : r_hi + (r - nt);
+      const int src = r < nt ? r_lo : r_hi - 1;
+      sm[dst * PITCH + c] = sm[src * PITCH + c];
+    }
+  }
+  cta_barrier();
 }
 
 // Stage a K x K filter asynchronously (4-byte cp.async; padding columns are
@@ -344,14 +382,17 @@ __device__ __forceinline__ void fwd_block(const TS* __restrict__ win,
     fwd_group<K, PY, REM, TS>(win + NG * A * Geo<K>::SP, f + NG * A * Geo<K>::KP, acc);
 }
 
-// Filter gradient of one DR-row dy block for the filter rows [a_lo, a_lo + nrows):
+// Filter gradient of one DR-row dy block for the NR filter rows [a_lo, a_lo + NR):
 // acc[s][b] += sum_{py, px} dy[py][px] * x~[py + a_lo + s][px + b]   (tile-local)
 // `dyb` points at the staged dy of block row 0 (lane column), `xw` at the
-// staged x row (block row 0 + a_lo) at the lane's first column.
-template <int K, int AT, int DYP, int DR, typename TS>
+// staged x row (block row 0 + a_lo) at the lane's first column.  NR is a
+// compile-time constant: the unrolled body has no data-dependent control flow
+// (with a run-time row count the accumulators live across guarded paths and
+// are copied where those paths merge).
+template <int K, int NR, int AT, int DYP, int DR, typename TS>
 __device__ __forceinline__ void dw_block(const TS* __restrict__ dyb,
-                                         const TS* __restrict__ xw, int nrows,
-                                         float (&acc)[AT][K]) {
+                                         const TS* __restrict__ xw, float (&acc)[AT][K]) {
+  static_assert(NR >= 1 && NR <= AT, "row count");
   using G = Geo<K>;
   float d[DR][4];
 #pragma unroll
@@ -363,20 +404,44 @@ __device__ __forceinline__ void dw_block(const TS* __restrict__ dyb,
     d[py][3] = t.w;
   }
 #pragma unroll
-  for (int ir = 0; ir < DR + AT - 1; ++ir) {
-    if (ir >= DR + nrows - 1) break;
+  for (int ir = 0; ir < DR + NR - 1; ++ir) {
     float buf[4 * G::NV];
     load_window_row<K, TS>(xw + ir * G::SP, buf);
 #pragma unroll
-    for (int s = 0; s < AT; ++s) {
+    for (int s = 0; s < NR; ++s) {
       const int py = ir - s;
-      if (py >= 0 && py < DR && s < nrows) {
+      if (py >= 0 && py < DR) {
 #pragma unroll
         for (int b = 0; b < K; ++b)
 #pragma unroll
           for (int px = 0; px < 4; ++px)
             acc[s][b] = fmaf(d[py][px], buf[G::OFF + px + b], acc[s][b]);
       }
+    }
+  }
+}
+
+// `nblocks` consecutive DR-row blocks for this warp's filter-row group of
+// `nrows` rows.  Splitting K rows into GT groups gives groups of AT or
+// AT - 1 rows; the branch on the (warp-uniform, fixed) row count is taken
+// once, outside the unrolled bodies.
+template <int K, int AT, int GT, int DYP, int DR, typename TS>
+__device__ __forceinline__ void dw_rows(const TS* __restrict__ dyb, const TS* __restrict__ xw,
+                                        int nblocks, int nrows, float (&acc)[AT][K]) {
+  constexpr int SP = Geo<K>::SP;
+  if constexpr (K % GT == 0) {
+#pragma unroll 1
+    for (int i = 0; i < nblocks; ++i)
+      dw_block<K, AT, AT, DYP, DR, TS>(dyb + i * DR * DYP, xw + i * DR * SP, acc);
+  } else {
+    if (nrows == AT) {
+#pragma unroll 1
+      for (int i = 0; i < nblocks; ++i)
+        dw_block<K, AT, AT, DYP, DR, TS>(dyb + i * DR * DYP, xw + i * DR * SP, acc);
+    } else {
+#pragma unroll 1
+      for (int i = 0; i < nblocks; ++i)
+        dw_block<K, AT - 1, AT, DYP, DR, TS>(dyb + i * DR * DYP, xw + i * DR * SP, acc);
     }
   }
 }
@@ -397,45 +462,74 @@ constexpr int bwd_block_rows() {
 // shared memory: while a tile is computed, the cp.async copies of the next
 // tile and of its plane's filter are in flight.  With flip = 1 the filter is
 // rotated by 180 degrees: that computes g (input gradient, zero border) from dy.
+constexpr int round_up(int v, int m) { return (v + m - 1) / m * m; }
+
 template <int K, int PY, typename T>
 struct FwdShape {
   using G = Geo<K>;
   static constexpr int TH = kWarps * PY;
-  static constexpr int TILE_BYTES = (TH + 2 * G::R) * G::SP * (int)sizeof(T);
-  static constexpr int STAGE_BYTES = G::WPAD * 4 + TILE_BYTES;  // filter, then tile
-  static constexpr int SM_BYTES = 2 * STAGE_BYTES;
+  static constexpr int ROWS = TH + 2 * G::R;
+  static constexpr int TILE_BYTES = ROWS * G::SP * (int)sizeof(T);
+  static constexpr int W_OFF = round_up(TILE_BYTES, 16);  // tile (TMA: 128-aligned), then filter
+  static constexpr int STAGE_BYTES = round_up(W_OFF + G::WPAD * 4, 128);
+  static constexpr int HEAD = 128;  // two mbarriers and the abort flag
+  static constexpr int SM_BYTES = HEAD + 2 * STAGE_BYTES;
+  static constexpr int SM_BYTES_1 = HEAD + STAGE_BYTES;  // one tile per CTA
 };
 
 template <typename T, int K, int PY>
-__global__ void __launch_bounds__(kThreads) dw_fwd_kernel(const T* __restrict__ x,
-                                                          const float* __restrict__ w,
-                                                          T* __restrict__ y, int C, int H, int W,
-                                                          int tiles_x, int tiles_y,
-                                                          int64_t num_tiles, int clamp, int vec,
-                                                          int flip) {
+__global__ void __launch_bounds__(kThreads) dw_fwd_kernel(
+    const __grid_constant__ CUtensorMap tmx, const T* __restrict__ x, const float* __restrict__ w,
+    T* __restrict__ y, int C, int H, int W, int tiles_x, int tiles_y, int64_t num_tiles, int clamp,
+    int vec, int flip, int use_tma, int* err) {
   using G = Geo<K>;
   using S = FwdShape<K, PY, T>;
   constexpr int TH = S::TH;
-  extern __shared__ __align__(16) float smem[];
+  extern __shared__ __align__(128) float smem[];
   char* sm = reinterpret_cast<char*>(smem);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm);
+  volatile int* s_abort = reinterpret_cast<volatile int*>(sm + 16);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-  auto stage = [&](int64_t t, int sb) {
-    const int tx = (int)(t % tiles_x);
+  auto coords = [&](int64_t t, int& ty0, int& tx0, int64_t& plane) {
+    tx0 = (int)(t % tiles_x) * kTileW;
     const int64_t t2 = t / tiles_x;
-    const int ty = (int)(t2 % tiles_y);
-    const int64_t plane = t2 / tiles_y;
-    float* sw = reinterpret_cast<float*>(sm + sb * S::STAGE_BYTES);
-    T* sx = reinterpret_cast<T*>(sm + sb * S::STAGE_BYTES + G::WPAD * 4);
+    ty0 = (int)(t2 % tiles_y) * TH;
+    plane = t2 / tiles_y;
+  };
+  auto stage = [&](int64_t t, int sb) {
+    int ty0, tx0;
+    int64_t plane;
+    coords(t, ty0, tx0, plane);
+    T* sx = reinterpret_cast<T*>(sm + S::HEAD + sb * S::STAGE_BYTES);
+    float* sw = reinterpret_cast<float*>(sm + S::HEAD + sb * S::STAGE_BYTES + S::W_OFF);
     stage_filter_async<K>(sw, w + (int64_t)(plane % C) * K * K, flip != 0, kThreads);
-    stage_tile<T, G::R, G::RP, G::SP>(sx, x + plane * (int64_t)H * W, H, W, ty * TH,
-                                      tx * kTileW, TH + 2 * G::R, clamp != 0, vec != 0);
+    if (use_tma) {
+      cp_async_commit();
+      if (threadIdx.x == 0) {
+        fence_proxy_async();
+        mbar_expect_tx(bars + sb, (uint32_t)S::TILE_BYTES);
+        tma_load_3d(sx, &tmx, tx0 - G::RP, ty0 - G::R, (int)plane, bars + sb);
+      }
+    } else {
+      stage_tile<T, G::R, G::RP, G::SP>(sx, x + plane * (int64_t)H * W, H, W, ty0, tx0, S::ROWS,
+                                        clamp != 0, vec != 0);
+    }
   };
 
+  if (threadIdx.x == 0) {
+    mbar_init(bars, 1);
+    mbar_init(bars + 1, 1);
+    *s_abort = 0;
+    mbar_init_fence();
+  }
+  cta_barrier();
   int64_t t = blockIdx.x;
   if (t >= num_tiles) return;
   stage(t, 0);
-  for (int sb = 0; t < num_tiles; t += gridDim.x, sb ^= 1) {
+  uint32_t phase = 0;  // bit s: parity of the next TMA completion on stage s
+  int sb = 0;
+  for (; t < num_tiles; t += gridDim.x, sb ^= 1) {
     const int64_t tn = t + gridDim.x;
     if (tn < num_tiles) {
       stage(tn, sb ^ 1);  // the other stage was released by the barrier below
@@ -443,46 +537,58 @@ __global__ void __launch_bounds__(kThreads) dw_fwd_kernel(const T* __restrict__ 
     } else {
       cp_async_wait_group<0>();
     }
+    if (use_tma) {
+      if (!mbar_wait(bars + sb, (phase >> sb) & 1u)) {
+        record_error(err, kDevErrTimeout);
+        *s_abort = 1;
+      }
+      phase ^= 1u << sb;
+    }
     cta_barrier();
-    const int tx = (int)(t % tiles_x);
-    const int64_t t2 = t / tiles_x;
-    const int ty = (int)(t2 % tiles_y);
-    const int64_t plane = t2 / tiles_y;
-    const float* sw = reinterpret_cast<const float*>(sm + sb * S::STAGE_BYTES);
-    const T* sx = reinterpret_cast<const T*>(sm + sb * S::STAGE_BYTES + G::WPAD * 4);
+    if (*s_abort) break;
+    int ty0, tx0;
+    int64_t plane;
+    coords(t, ty0, tx0, plane);
+    T* sx = reinterpret_cast<T*>(sm + S::HEAD + sb * S::STAGE_BYTES);
+    const float* sw = reinterpret_cast<const float*>(sm + S::HEAD + sb * S::STAGE_BYTES + S::W_OFF);
+    if (use_tma && clamp &&
+        (ty0 - G::R < 0 || ty0 + TH + G::R > H || tx0 - G::RP < 0 || tx0 + kTileW + G::RP > W))
+      clamp_fix<T, G::SP, kThreads>(sx, H, W, ty0, tx0, G::R, G::RP, S::ROWS);
     float acc[PY][4];
     fwd_block<K, PY, T>(sx + warp * PY * G::SP + 4 * lane, sw, acc);
-    store_block<T, PY>(y + plane * (int64_t)H * W, H, W, ty * TH + warp * PY,
-                       tx * kTileW + 4 * lane, vec != 0, acc);
+    store_block<T, PY>(y + plane * (int64_t)H * W, H, W, ty0 + warp * PY, tx0 + 4 * lane,
+                       vec != 0, acc);
     cta_barrier();  // every warp is done with stage sb before it is refilled
   }
+  cp_async_wait_group<0>();
+  // after an abort: let a TMA load still in flight land (bounded) before exiting
+  if (*s_abort && use_tma && t + gridDim.x < num_tiles) mbar_wait(bars + (sb ^ 1), (phase >> (sb ^ 1)) & 1u);
 }
 
 // -------------------------------------------------------------- backward
-// MODE 0: fused; warps 0-3 write g (= dx for the zero border) from the staged
-//         dy tile, warps 4-7 accumulate dw from the staged x and dy tiles.
-// MODE 1: filter gradient only; all 8 warps accumulate dw (dy staged without
-//         a halo).
-// A CTA owns `tpc` consecutive 64 x 128 tiles of one plane and writes one
-// K*K vector of FP32 partial sums to partials[blockIdx.x].
-template <int K, int MODE, typename T>
+// Fused backward: warps 0-3 write g (= dx for the zero border) from the staged
+// dy tile, warps 4-7 accumulate dw from the staged x and dy tiles.  A CTA owns
+// `tpc` consecutive 64 x 128 tiles of one plane and writes one K*K vector of
+// FP32 partial sums to partials[blockIdx.x].  FP32 planes with a 16-byte row
+// stride are staged by two TMA loads per tile (zeros outside the image; under
+// the clamp border the x tile of an edge tile then gets clamp_fix), others by
+// cp.async with the border applied.
+template <int K, typename T>
 struct BwdShape {
   using G = Geo<K>;
-  static constexpr int NDX = MODE == 0 ? 4 : 0;
+  static constexpr int NDX = 4;
   static constexpr int NDW = kWarps - NDX;
   static constexpr int GT = dw_groups<K>();
   static constexpr int WPG = NDW / GT;              // warps per filter-row group
   static constexpr int AT = (K + GT - 1) / GT;      // max filter rows per group
   static constexpr int DW_ROWS = kBwdTileH / WPG;   // tile rows per dw warp
-  static constexpr int X_ROWS = kBwdTileH + 2 * G::R;
-  static constexpr int DY_HR = MODE == 0 ? G::R : 0;
-  static constexpr int DY_HC = MODE == 0 ? G::RP : 0;
-  static constexpr int DY_P = MODE == 0 ? G::SP : kTileW;
-  static constexpr int DY_ROWS = kBwdTileH + 2 * DY_HR;
-  // byte offsets: staged tiles in the storage type, filter and reduction FP32
-  static constexpr int SM_X = 0;
-  static constexpr int SM_DY = X_ROWS * G::SP * (int)sizeof(T);
-  static constexpr int SM_W = SM_DY + DY_ROWS * DY_P * (int)sizeof(T);
+  static constexpr int ROWS = kBwdTileH + 2 * G::R;  // x and dy tiles, both with the halo
+  static constexpr int TILE_BYTES = ROWS * G::SP * (int)sizeof(T);
+  // byte offsets: mbarrier and abort flag, staged tiles (TMA destinations
+  // 128-byte aligned), flipped filter and reduction in FP32
+  static constexpr int SM_X = 128;
+  static constexpr int SM_DY = SM_X + round_up(TILE_BYTES, 128);
+  static constexpr int SM_W = SM_DY + round_up(TILE_BYTES, 16);
   static constexpr int SM_RED = SM_W + G::WPAD * 4;
   static constexpr int SM_BYTES = SM_RED + NDW * AT * K * 4;
   static_assert(NDW % GT == 0, "filter-row groups must divide the dw warps");
@@ -499,16 +605,20 @@ constexpr int bwd_min_ctas() {
   return K <= 5 ? 3 : 2;
 }
 
-template <typename T, int K, int MODE>
+template <typename T, int K>
 __global__ void __launch_bounds__(kThreads, bwd_min_ctas<T, K>())
-    dw_bwd_kernel(const T* __restrict__ x, const T* __restrict__ dy, const float* __restrict__ w,
-                  T* __restrict__ dx, float* __restrict__ partials, int C, int H, int W,
-                  int tiles_x, int tiles_per_plane, int chunks_per_plane, int tpc, int clamp,
-                  int vec) {
+    dw_bwd_kernel(const __grid_constant__ CUtensorMap tmx,
+                  const __grid_constant__ CUtensorMap tmdy, const T* __restrict__ x,
+                  const T* __restrict__ dy, const float* __restrict__ w, T* __restrict__ dx,
+                  float* __restrict__ partials, int C, int H, int W, int tiles_x,
+                  int tiles_per_plane, int chunks_per_plane, int tpc, int clamp, int vec,
+                  int use_tma, int* err) {
   using G = Geo<K>;
-  using S = BwdShape<K, MODE, T>;
-  extern __shared__ __align__(16) float smem[];
+  using S = BwdShape<K, T>;
+  extern __shared__ __align__(128) float smem[];
   char* sm = reinterpret_cast<char*>(smem);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sm);
+  volatile int* s_abort = reinterpret_cast<volatile int*>(sm + 8);
   T* sm_x = reinterpret_cast<T*>(sm + S::SM_X);
   T* sm_dy = reinterpret_cast<T*>(sm + S::SM_DY);
   float* sm_w = reinterpret_cast<float*>(sm + S::SM_W);
@@ -523,26 +633,60 @@ __global__ void __launch_bounds__(kThreads, bwd_min_ctas<T, K>())
   const T* xp = x + plane_off;
   const T* dyp = dy + plane_off;
 
-  if (MODE == 0) stage_filter<K>(sm_w, w + (int64_t)c * K * K, true, kThreads);
+  // rotated filter; its copies complete with the first tile's
+  stage_filter_async<K>(sm_w, w + (int64_t)c * K * K, true, kThreads);
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    *s_abort = 0;
+    mbar_init_fence();
+  }
+  uint32_t phase = 0;
+  // Stage tile (ty0, tx0) after every warp is done with the previous one;
+  // false if a TMA wait gave up (every thread then leaves its tile loop).
+  auto stage = [&](int ty0, int tx0) -> bool {
+    cta_barrier();
+    if (use_tma) {
+      cp_async_commit();
+      if (threadIdx.x == 0) {
+        fence_proxy_async();
+        mbar_expect_tx(bar, (uint32_t)(2 * S::TILE_BYTES));
+        tma_load_3d(sm_x, &tmx, tx0 - G::RP, ty0 - G::R, (int)plane, bar);
+        tma_load_3d(sm_dy, &tmdy, tx0 - G::RP, ty0 - G::R, (int)plane, bar);
+      }
+      cp_async_wait_all();
+      if (mbar_wait(bar, phase))
+        phase ^= 1u;
+      else {
+        record_error(err, kDevErrTimeout);
+        *s_abort = 1;
+      }
+      cta_barrier();
+      if (*s_abort) return false;
+      if (clamp && (ty0 - G::R < 0 || ty0 + kBwdTileH + G::R > H || tx0 - G::RP < 0 ||
+                    tx0 + kTileW + G::RP > W))
+        clamp_fix<T, G::SP, kThreads>(sm_x, H, W, ty0, tx0, G::R, G::RP, S::ROWS);
+    } else {
+      stage_tile<T, G::R, G::RP, G::SP>(sm_x, xp, H, W, ty0, tx0, S::ROWS, clamp != 0,
+                                        vec != 0);
+      stage_tile<T, G::R, G::RP, G::SP>(sm_dy, dyp, H, W, ty0, tx0, S::ROWS, false, vec != 0);
+      stage_wait();
+    }
+    return true;
+  };
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   if (warp < S::NDX) {
-    // ---- input-gradient warps: 16 rows each, two passes of 8 rows
+    // ---- input-gradient warps: 16 rows each, in blocks of BR rows
     for (int t = t_begin; t < t_end; ++t) {
       const int ty0 = (t / tiles_x) * kBwdTileH, tx0 = (t % tiles_x) * kTileW;
-      cta_barrier();
-      stage_tile<T, G::R, G::RP, G::SP>(sm_x, xp, H, W, ty0, tx0, S::X_ROWS, clamp != 0,
-                                        vec != 0);
-      stage_tile<T, S::DY_HR, S::DY_HC, S::DY_P>(sm_dy, dyp, H, W, ty0, tx0, S::DY_ROWS, false,
-                                                 vec != 0);
-      stage_wait();
+      if (!stage(ty0, tx0)) break;
       constexpr int BR = bwd_block_rows<K>();
 #pragma unroll 1
       for (int pass = 0; pass < 16 / BR; ++pass) {
         const int r0 = warp * 16 + pass * BR;
         float acc[BR][4];
-        fwd_block<K, BR, T>(sm_dy + r0 * S::DY_P + 4 * lane, sm_w, acc);
+        fwd_block<K, BR, T>(sm_dy + r0 * G::SP + 4 * lane, sm_w, acc);
         store_block<T, BR>(dx + plane_off, H, W, ty0 + r0, tx0 + 4 * lane, vec != 0, acc);
       }
     }
@@ -562,19 +706,12 @@ __global__ void __launch_bounds__(kThreads, bwd_min_ctas<T, K>())
       for (int b = 0; b < K; ++b) acc[s][b] = 0.f;
     for (int t = t_begin; t < t_end; ++t) {
       const int ty0 = (t / tiles_x) * kBwdTileH, tx0 = (t % tiles_x) * kTileW;
-      cta_barrier();
-      stage_tile<T, G::R, G::RP, G::SP>(sm_x, xp, H, W, ty0, tx0, S::X_ROWS, clamp != 0,
-                                        vec != 0);
-      stage_tile<T, S::DY_HR, S::DY_HC, S::DY_P>(sm_dy, dyp, H, W, ty0, tx0, S::DY_ROWS, false,
-                                                 vec != 0);
-      stage_wait();
+      if (!stage(ty0, tx0)) break;
       constexpr int BR = bwd_block_rows<K>();
-#pragma unroll 1
-      for (int r0 = part * S::DW_ROWS; r0 < (part + 1) * S::DW_ROWS; r0 += BR) {
-        dw_block<K, S::AT, S::DY_P, BR, T>(
-            sm_dy + (r0 + S::DY_HR) * S::DY_P + S::DY_HC + 4 * lane,
-            sm_x + (r0 + a_lo) * G::SP + 4 * lane, nrows, acc);
-      }
+      const int r0 = part * S::DW_ROWS;
+      dw_rows<K, S::AT, S::GT, G::SP, BR, T>(sm_dy + (r0 + G::R) * G::SP + G::RP + 4 * lane,
+                                             sm_x + (r0 + a_lo) * G::SP + 4 * lane,
+                                             S::DW_ROWS / BR, nrows, acc);
     }
     // warp reduction (fixed butterfly order), one row of sm_red per warp
     cta_barrier();
@@ -599,6 +736,204 @@ __global__ void __launch_bounds__(kThreads, bwd_min_ctas<T, K>())
     for (int p = 0; p < S::WPG; ++p) sum += sm_red[((p * S::GT + g) * S::AT + s) * K + b];
     partials[(int64_t)blockIdx.x * K * K + k] = sum;
   }
+  cp_async_wait_all();
+  if (*s_abort && use_tma) mbar_wait(bar, phase);  // let a late TMA load land (bounded)
+}
+
+// ------------------------------------------------------- filter gradient
+// The filter gradient alone (Eq. 3's adjoint with respect to the filter):
+// dw[c][a][b] = sum over n, i, j of dy[n][c][i][j] * xs[n][c][i + a - r][j + b - r],
+// xs the border-extended input.  One CTA of 16 warps per SM, persistent over
+// chunks of `tpc` consecutive 64 x 128 tiles of one plane (chunk q runs on
+// CTA q mod gridDim.x).  NS shared-memory stages hold {x tile with halo, dy
+// tile}; the copies of the tile NS - 1 items ahead are in flight while the
+// current one is reduced, across chunk boundaries too.  For FP32 rows with a
+// 16-byte stride a stage is filled by two TMA tensor loads issued by one
+// thread (out-of-image reads arrive as zeros: the zero border; under the
+// clamp border the edge tiles then get clamp_fix); otherwise by every
+// thread's cp.async copies with the border applied.  Tap rows are split into GT groups; warp w takes group w / WPG and
+// tile rows part w mod WPG, so each of the SM's four schedulers (w mod 4)
+// holds one warp of every group.  At the end of a chunk the warps' sums
+// (fixed butterfly order) and then the group's warps (fixed order) give the
+// chunk's partial for every tap.
+constexpr int kFilterWarps = 16;
+constexpr int kFilterThreads = kFilterWarps * 32;
+constexpr int kFilterTileH = 64;
+static_assert(kFilterTileH == kBwdTileH, "both filter-gradient kernels share the chunk layout");
+
+template <int K, typename T>
+struct FilterShape {
+  using G = Geo<K>;
+  static constexpr int GT = dw_groups<K>();
+  static constexpr int WPG = kFilterWarps / GT;
+  static constexpr int AT = (K + GT - 1) / GT;
+  static constexpr int ROWS = kFilterTileH / WPG;  // tile rows per warp
+  static constexpr int DR = 4;                     // dy rows per unrolled block
+  static constexpr int X_ROWS = kFilterTileH + 2 * G::R;
+  static constexpr int X_BYTES = X_ROWS * G::SP * (int)sizeof(T);
+  static constexpr int DY_BYTES = kFilterTileH * kTileW * (int)sizeof(T);
+  static constexpr int DY_OFF = round_up(X_BYTES, 128);  // TMA destinations: 128-byte aligned
+  static constexpr int STAGE_BYTES = round_up(DY_OFF + DY_BYTES, 128);
+  static constexpr int NS = K <= 9 ? 3 : 2;
+  static constexpr int SM_RED = NS * STAGE_BYTES;
+  static constexpr int SM_BAR = round_up(SM_RED + kFilterWarps * AT * K * 4, 8);
+  static constexpr int SM_BYTES = SM_BAR + NS * 8 + 8;  // mbarriers, abort flag
+  static_assert(kFilterWarps % GT == 0 && ROWS % DR == 0, "warps own whole row blocks");
+  static_assert(SM_BYTES <= 227 * 1024, "shared memory");
+};
+
+template <typename T, int K>
+__global__ void __launch_bounds__(kFilterThreads, 1)
+    dw_filter_kernel(const __grid_constant__ CUtensorMap tmx,
+                     const __grid_constant__ CUtensorMap tmdy, const T* __restrict__ x,
+                     const T* __restrict__ dy, float* __restrict__ partials, int H, int W,
+                     int tiles_x, int tiles_per_plane, int chunks_per_plane, int tpc,
+                     int64_t num_chunks, int clamp, int vec, int use_tma, int* err) {
+  using G = Geo<K>;
+  using S = FilterShape<K, T>;
+  extern __shared__ __align__(128) float smem[];
+  char* sm = reinterpret_cast<char*>(smem);
+  float* sm_red = reinterpret_cast<float*>(sm + S::SM_RED);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + S::SM_BAR);
+  volatile int* s_abort = reinterpret_cast<volatile int*>(sm + S::SM_BAR + S::NS * 8);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = warp / S::WPG, part = warp % S::WPG;
+  const int a_lo = group_lo(g, K, S::GT);
+  const int nrows = group_lo(g + 1, K, S::GT) - a_lo;
+
+  // (chunk, tile) items in execution order; t < t_end while valid
+  struct Item {
+    int64_t q;
+    int t, t_end;
+  };
+  auto first_tile = [&](Item& it) {
+    const int ch = (int)(it.q % chunks_per_plane);
+    it.t = ch * tpc;
+    it.t_end = min(it.t + tpc, tiles_per_plane);
+  };
+  auto advance = [&](Item& it) {
+    if (++it.t == it.t_end) {
+      it.q += gridDim.x;
+      if (it.q < num_chunks) first_tile(it);
+    }
+  };
+  // the x halo of a tile reaches outside the image (same answer for every thread)
+  auto at_edge = [&](const Item& it) {
+    const int ty0 = (it.t / tiles_x) * kFilterTileH, tx0 = (it.t % tiles_x) * kTileW;
+    return ty0 - G::R < 0 || ty0 + kFilterTileH + G::R > H || tx0 - G::RP < 0 ||
+           tx0 + kTileW + G::RP > W;
+  };
+  auto stage = [&](const Item& it, int sb) {
+    const int64_t plane = it.q / chunks_per_plane;
+    const int ty0 = (it.t / tiles_x) * kFilterTileH, tx0 = (it.t % tiles_x) * kTileW;
+    T* sx = reinterpret_cast<T*>(sm + sb * S::STAGE_BYTES);
+    T* sdy = reinterpret_cast<T*>(sm + sb * S::STAGE_BYTES + S::DY_OFF);
+    if (use_tma) {
+      if (threadIdx.x == 0) {
+        fence_proxy_async();
+        mbar_expect_tx(bars + sb, (uint32_t)(S::X_BYTES + S::DY_BYTES));
+        tma_load_3d(sx, &tmx, tx0 - G::RP, ty0 - G::R, (int)plane, bars + sb);
+        tma_load_3d(sdy, &tmdy, tx0, ty0, (int)plane, bars + sb);
+      }
+    } else {
+      const int64_t off = plane * (int64_t)H * W;
+      stage_tile<T, G::R, G::RP, G::SP, kFilterThreads, false>(sx, x + off, H, W, ty0, tx0,
+                                                               S::X_ROWS, clamp != 0, vec != 0);
+      stage_tile<T, 0, 0, kTileW, kFilterThreads, false>(sdy, dy + off, H, W, ty0, tx0,
+                                                         kFilterTileH, false, vec != 0);
+    }
+  };
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < S::NS; ++i) mbar_init(bars + i, 1);
+    *s_abort = 0;
+    mbar_init_fence();
+  }
+  cta_barrier();
+
+  Item pf{(int64_t)blockIdx.x, 0, 0};
+  if (pf.q >= num_chunks) return;
+  first_tile(pf);
+  Item cs = pf;
+  uint32_t phase = 0;    // bit s: parity of the next TMA completion on stage s
+  uint32_t pending = 0;  // bit s: a TMA load into stage s is in flight
+  // prologue: the first NS - 1 items (one commit group per item, empty past the end)
+#pragma unroll
+  for (int i = 0; i < S::NS - 1; ++i) {
+    if (pf.q < num_chunks) {
+      if (use_tma) pending |= 1u << i;
+      stage(pf, i);
+      advance(pf);
+    }
+    cp_async_commit();
+  }
+
+  float acc[S::AT][K];
+#pragma unroll
+  for (int s = 0; s < S::AT; ++s)
+#pragma unroll
+    for (int b = 0; b < K; ++b) acc[s][b] = 0.f;
+
+  for (int sb = 0; cs.q < num_chunks; sb = (sb + 1 == S::NS) ? 0 : sb + 1) {
+    // refill the stage released at the end of the previous item
+    if (pf.q < num_chunks) {
+      const int ps = sb == 0 ? S::NS - 1 : sb - 1;
+      if (use_tma) pending |= 1u << ps;
+      stage(pf, ps);
+      advance(pf);
+    }
+    cp_async_commit();
+    cp_async_wait_group<S::NS - 1>();  // the current item's cp.async copies have landed
+    if (pending & (1u << sb)) {
+      if (!mbar_wait(bars + sb, (phase >> sb) & 1u)) {
+        record_error(err, kDevErrTimeout);
+        *s_abort = 1;
+      }
+      phase ^= 1u << sb;
+      pending &= ~(1u << sb);
+    }
+    cta_barrier();
+    if (*s_abort) break;
+    T* sx = reinterpret_cast<T*>(sm + sb * S::STAGE_BYTES);
+    const T* sdy = reinterpret_cast<const T*>(sm + sb * S::STAGE_BYTES + S::DY_OFF);
+    if (use_tma && clamp && at_edge(cs))
+      clamp_fix<T, G::SP, kFilterThreads>(sx, H, W, (cs.t / tiles_x) * kFilterTileH,
+                                          (cs.t % tiles_x) * kTileW, G::R, G::RP, S::X_ROWS);
+    dw_rows<K, S::AT, S::GT, kTileW, S::DR, T>(sdy + part * S::ROWS * kTileW + 4 * lane,
+                                               sx + (part * S::ROWS + a_lo) * G::SP + 4 * lane,
+                                               S::ROWS / S::DR, nrows, acc);
+    const bool chunk_end = cs.t + 1 == cs.t_end;
+    if (chunk_end) {
+#pragma unroll
+      for (int s = 0; s < S::AT; ++s)
+#pragma unroll
+        for (int b = 0; b < K; ++b) {
+          float v = acc[s][b];
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+          if (lane == 0) sm_red[(warp * S::AT + s) * K + b] = v;
+          acc[s][b] = 0.f;
+        }
+    }
+    cta_barrier();  // stage sb is free again; sm_red is complete
+    if (chunk_end) {
+      for (int k = threadIdx.x; k < K * K; k += kFilterThreads) {
+        const int a = k / K, b = k - (k / K) * K;
+        int gg = 0;
+        while (gg + 1 < S::GT && group_lo(gg + 1, K, S::GT) <= a) ++gg;
+        const int s = a - group_lo(gg, K, S::GT);
+        float sum = 0.f;
+        for (int p = 0; p < S::WPG; ++p) sum += sm_red[((gg * S::WPG + p) * S::AT + s) * K + b];
+        partials[cs.q * K * K + k] = sum;
+      }
+      // sm_red is rewritten no earlier than the next chunk end, after another barrier
+    }
+    advance(cs);
+  }
+  cp_async_wait_group<0>();
+  // after an abort: let the TMA loads still in flight land (bounded) before exiting
+  for (int s = 0; s < S::NS; ++s)
+    if (pending & (1u << s)) mbar_wait(bars + s, (phase >> s) & 1u);
 }
 
 }  // namespace giga

@@ -18,12 +18,23 @@ template <int K>
 cudaError_t dw_fwd_launch(const DwArgs& a, const DwConfig& cfg, bool input_grad,
                           cudaStream_t st);
 
-// Backward tile pass: mode 0 = fused g + filter partials, mode 1 = filter
-// partials only.  Writes partials[planes * chunks][K*K].
+// Fused backward tile pass: g (the input gradient before the clamp edge
+// fold) and the filter partials[planes * chunks][K*K].
 template <int K>
-cudaError_t dw_bwd_launch(const DwArgs& a, const DwConfig& cfg, int mode, cudaStream_t st);
+cudaError_t dw_bwd_launch(const DwArgs& a, const DwConfig& cfg, cudaStream_t st);
 
-// Number of CTAs per plane the backward pass uses for `tiles_per_cta`.
+// Filter gradient alone (persistent multi-stage kernel).  Writes
+// partials[planes * chunks][K*K] in the same layout as dw_bwd_launch.
+template <int K>
+cudaError_t dw_filter_launch(const DwArgs& a, const DwConfig& cfg, cudaStream_t st);
+
+// Device error word of the depthwise kernels (nonzero after a bounded wait
+// gave up) for the current device; nullptr if unavailable.
+int* dw_error_word();
+// Synchronise `st`, read and clear that word.
+cudaError_t dw_take_error(cudaStream_t st, int* code);
+
+// Number of tile chunks per plane the backward pass uses for `tiles_per_cta`.
 int64_t dw_bwd_chunks_per_plane(int64_t H, int64_t W, int tiles_per_cta);
 
 // Clamp border: overwrite the edge pixels of dx with the exact adjoint.
@@ -36,8 +47,10 @@ cudaError_t dw_finalize_launch(const DwArgs& a, int64_t chunks_per_plane, cudaSt
   extern template cudaError_t dw_fwd_launch<K>(const DwArgs&, const DwConfig&, bool,      \
                                                cudaStream_t);
 #define GIGA_DW_EXTERN_BWD(K)                                                              \
-  extern template cudaError_t dw_bwd_launch<K>(const DwArgs&, const DwConfig&, int,       \
-                                               cudaStream_t);
+  extern template cudaError_t dw_bwd_launch<K>(const DwArgs&, const DwConfig&,            \
+                                               cudaStream_t);                              \
+  extern template cudaError_t dw_filter_launch<K>(const DwArgs&, const DwConfig&,         \
+                                                  cudaStream_t);
 GIGA_DW_EXTERN(1) GIGA_DW_EXTERN(3) GIGA_DW_EXTERN(5) GIGA_DW_EXTERN(7)
 GIGA_DW_EXTERN(9) GIGA_DW_EXTERN(11) GIGA_DW_EXTERN(13) GIGA_DW_EXTERN(15)
 GIGA_DW_EXTERN(17) GIGA_DW_EXTERN(19) GIGA_DW_EXTERN(21) GIGA_DW_EXTERN(23)

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <algorithm>
+#include <cstring>
 
 #include "dw_kernels.cuh"
 #include "dw_launch.h"
@@ -23,7 +24,7 @@ static cudaError_t fwd_impl(const DwArgs& a, bool input_grad, bool persistent, c
   const int64_t tiles_y = (a.H + S::TH - 1) / S::TH;
   const int64_t tiles = a.N * a.C * tiles_x * tiles_y;
   int64_t grid = tiles;
-  size_t smem = (size_t)S::STAGE_BYTES;
+  size_t smem = (size_t)S::SM_BYTES_1;
   if (persistent) {
     smem = (size_t)S::SM_BYTES;
     static int ctas_per_sm[64] = {};
@@ -43,10 +44,16 @@ static cudaError_t fwd_impl(const DwArgs& a, bool input_grad, bool persistent, c
   if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
   const T* in = static_cast<const T*>(input_grad ? a.dy : a.x);
   T* out = static_cast<T*>(input_grad ? a.dx : a.y);
-  kern<<<(unsigned)grid, kThreads, smem, st>>>(in, a.w, out, (int)a.C, (int)a.H, (int)a.W,
+  // TMA staging for FP32 rows with a 16-byte stride from a 16-byte aligned base
+  CUtensorMap tm;
+  std::memset(&tm, 0, sizeof(tm));
+  int use_tma = 0;
+  if (sizeof(T) == 4 && a.vec)
+    use_tma = make_plane_map_f32(&tm, in, a.W, a.H, a.N * a.C, Geo<K>::SP, S::ROWS);
+  kern<<<(unsigned)grid, kThreads, smem, st>>>(tm, in, a.w, out, (int)a.C, (int)a.H, (int)a.W,
                                                (int)tiles_x, (int)tiles_y, tiles,
                                                input_grad ? 0 : a.border, a.vec,
-                                               input_grad ? 1 : 0);
+                                               input_grad ? 1 : 0, use_tma, dw_error_word());
   note_launch();
   return cudaGetLastError();
 }
@@ -63,41 +70,99 @@ cudaError_t dw_fwd_launch(const DwArgs& a, const DwConfig& cfg, bool input_grad,
              : fwd_impl<__nv_bfloat16, K, 8>(a, input_grad, pers, st);
 }
 
-template <typename T, int K, int MODE>
+template <typename T, int K>
 static cudaError_t bwd_impl(const DwArgs& a, const DwConfig& cfg, cudaStream_t st) {
-  using S = BwdShape<K, MODE, T>;
+  using S = BwdShape<K, T>;
   const size_t smem = (size_t)S::SM_BYTES;
-  auto kern = dw_bwd_kernel<T, K, MODE>;
-  cudaError_t e = set_smem_once<dw_bwd_kernel<T, K, MODE>>(smem);
+  auto kern = dw_bwd_kernel<T, K>;
+  cudaError_t e = set_smem_once<dw_bwd_kernel<T, K>>(smem);
   if (e != cudaSuccess) return e;
   const int64_t tiles_x = (a.W + kTileW - 1) / kTileW;
   const int64_t tiles_y = (a.H + kBwdTileH - 1) / kBwdTileH;
   const int64_t tpp = tiles_x * tiles_y;
   const int64_t chunks = dw_bwd_chunks_per_plane(a.H, a.W, cfg.tiles_per_cta);
   const int64_t grid = a.N * a.C * chunks;
+  CUtensorMap tmx, tmdy;
+  std::memset(&tmx, 0, sizeof(tmx));
+  std::memset(&tmdy, 0, sizeof(tmdy));
+  int use_tma = 0;
+  if (sizeof(T) == 4 && a.vec)
+    use_tma = make_plane_map_f32(&tmx, a.x, a.W, a.H, a.N * a.C, Geo<K>::SP, S::ROWS) &&
+              make_plane_map_f32(&tmdy, a.dy, a.W, a.H, a.N * a.C, Geo<K>::SP, S::ROWS);
   kern<<<(unsigned)grid, kThreads, smem, st>>>(
-      static_cast<const T*>(a.x), static_cast<const T*>(a.dy), a.w, static_cast<T*>(a.dx),
-      a.partials, (int)a.C, (int)a.H, (int)a.W, (int)tiles_x, (int)tpp, (int)chunks,
-      cfg.tiles_per_cta, a.border, a.vec);
+      tmx, tmdy, static_cast<const T*>(a.x), static_cast<const T*>(a.dy), a.w,
+      static_cast<T*>(a.dx), a.partials, (int)a.C, (int)a.H, (int)a.W, (int)tiles_x, (int)tpp,
+      (int)chunks, cfg.tiles_per_cta, a.border, a.vec, use_tma, dw_error_word());
   note_launch();
   return cudaGetLastError();
 }
 
 template <int K>
-cudaError_t dw_bwd_launch(const DwArgs& a, const DwConfig& cfg, int mode, cudaStream_t st) {
+cudaError_t dw_bwd_launch(const DwArgs& a, const DwConfig& cfg, cudaStream_t st) {
   if constexpr (K > kMaxKFilter) {
     return cudaErrorInvalidValue;
   } else {
-    if (a.dtype == 0)
-      return mode == 0 ? bwd_impl<float, K, 0>(a, cfg, st) : bwd_impl<float, K, 1>(a, cfg, st);
-    return mode == 0 ? bwd_impl<__nv_bfloat16, K, 0>(a, cfg, st)
-                     : bwd_impl<__nv_bfloat16, K, 1>(a, cfg, st);
+    return a.dtype == 0 ? bwd_impl<float, K>(a, cfg, st) : bwd_impl<__nv_bfloat16, K>(a, cfg, st);
+  }
+}
+
+template <typename T, int K>
+static cudaError_t filter_impl(const DwArgs& a, const DwConfig& cfg, cudaStream_t st) {
+  using S = FilterShape<K, T>;
+  const size_t smem = (size_t)S::SM_BYTES;
+  auto kern = dw_filter_kernel<T, K>;
+  cudaError_t e = set_smem_once<dw_filter_kernel<T, K>>(smem);
+  if (e != cudaSuccess) return e;
+  static int ctas_per_sm[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int& per_sm = ctas_per_sm[dev & 63];
+  if (per_sm == 0) {
+    int v = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kern, kFilterThreads, smem) !=
+            cudaSuccess ||
+        v < 1)
+      v = 1;
+    per_sm = v;
+  }
+  const int64_t tiles_x = (a.W + kTileW - 1) / kTileW;
+  const int64_t tiles_y = (a.H + kFilterTileH - 1) / kFilterTileH;
+  const int64_t chunks = dw_bwd_chunks_per_plane(a.H, a.W, cfg.tiles_per_cta);
+  const int64_t num_chunks = a.N * a.C * chunks;
+  const int64_t grid = std::min<int64_t>(num_chunks, (int64_t)per_sm * sm_count());
+  // TMA staging: FP32 rows with a 16-byte stride from 16-byte aligned bases
+  // (the vectorised-access condition); otherwise cp.async staging.
+  CUtensorMap tmx, tmdy;
+  std::memset(&tmx, 0, sizeof(tmx));
+  std::memset(&tmdy, 0, sizeof(tmdy));
+  int use_tma = 0;
+  if (sizeof(T) == 4 && a.vec) {
+    use_tma = make_plane_map_f32(&tmx, a.x, a.W, a.H, a.N * a.C, Geo<K>::SP, S::X_ROWS) &&
+              make_plane_map_f32(&tmdy, a.dy, a.W, a.H, a.N * a.C, kTileW, kFilterTileH);
+  }
+  int* err = dw_error_word();
+  kern<<<(unsigned)grid, kFilterThreads, smem, st>>>(
+      tmx, tmdy, static_cast<const T*>(a.x), static_cast<const T*>(a.dy), a.partials, (int)a.H,
+      (int)a.W, (int)tiles_x, (int)(tiles_x * tiles_y), (int)chunks, cfg.tiles_per_cta,
+      num_chunks, a.border, a.vec, use_tma, err);
+  note_launch();
+  return cudaGetLastError();
+}
+
+template <int K>
+cudaError_t dw_filter_launch(const DwArgs& a, const DwConfig& cfg, cudaStream_t st) {
+  if constexpr (K > kMaxKFilter) {
+    return cudaErrorInvalidValue;
+  } else {
+    return a.dtype == 0 ? filter_impl<float, K>(a, cfg, st)
+                        : filter_impl<__nv_bfloat16, K>(a, cfg, st);
   }
 }
 
 #define GIGA_DW_INSTANTIATE(K)                                                            \
   template cudaError_t dw_fwd_launch<K>(const DwArgs&, const DwConfig&, bool, cudaStream_t);
 #define GIGA_DW_INSTANTIATE_BWD(K)                                                        \
-  template cudaError_t dw_bwd_launch<K>(const DwArgs&, const DwConfig&, int, cudaStream_t);
+  template cudaError_t dw_bwd_launch<K>(const DwArgs&, const DwConfig&, cudaStream_t);      \
+  template cudaError_t dw_filter_launch<K>(const DwArgs&, const DwConfig&, cudaStream_t);
 
 }  // namespace giga

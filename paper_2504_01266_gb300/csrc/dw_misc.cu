@@ -9,6 +9,33 @@
 
 namespace giga {
 
+// Device error word of the depthwise kernels (bounded TMA waits).
+static __device__ int g_dw_err;
+
+int* dw_error_word() {
+  static int* cached[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  if (!cached[dev]) {
+    int* p = nullptr;
+    if (cudaGetSymbolAddress(reinterpret_cast<void**>(&p), g_dw_err) != cudaSuccess) return nullptr;
+    cached[dev] = p;
+  }
+  return cached[dev];
+}
+
+cudaError_t dw_take_error(cudaStream_t st, int* code) {
+  *code = 0;
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return e;
+  int* err = dw_error_word();
+  if (!err) return cudaErrorInvalidSymbol;
+  e = cudaMemcpy(code, err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return e;
+  const int zero = 0;
+  return cudaMemcpy(err, &zero, sizeof(int), cudaMemcpyHostToDevice);
+}
+
 int64_t dw_bwd_chunks_per_plane(int64_t H, int64_t W, int tiles_per_cta) {
   const int64_t tiles = ((W + kTileW - 1) / kTileW) * ((H + kBwdTileH - 1) / kBwdTileH);
   return (tiles + tiles_per_cta - 1) / tiles_per_cta;

@@ -157,10 +157,10 @@ __device__ __forceinline__ void rag_chunk(const RagParams& p, const RagChunk& ch
       stage_wait();
       if (do_dw) {
         constexpr int BR = bwd_block_rows<K>();
-#pragma unroll 1
-        for (int r0 = part * S::DW_ROWS; r0 < (part + 1) * S::DW_ROWS; r0 += BR)
-          dw_block<K, S::AT, G::SP, BR, T>(sm_dy + (r0 + G::R) * G::SP + G::RP + 4 * lane,
-                                           sm_x + (r0 + a_lo) * G::SP + 4 * lane, nrows, acc);
+        const int r0 = part * S::DW_ROWS;
+        dw_rows<K, S::AT, S::GT, G::SP, BR, T>(sm_dy + (r0 + G::R) * G::SP + G::RP + 4 * lane,
+                                               sm_x + (r0 + a_lo) * G::SP + 4 * lane,
+                                               S::DW_ROWS / BR, nrows, acc);
       }
     }
     cta_barrier();

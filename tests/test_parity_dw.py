@@ -139,35 +139,52 @@ def test_misaligned_view_uses_scalar_path(giga):
     assert normwise(to_np(y), oracle.dw_fwd(x.numpy(), w.numpy(), oracle.CLAMP)) <= FP32_TOL
 
 
-def _force_fwd_candidate(tmp_path, shape, K, border, dtype, cand):
-    """Pin the forward and input-gradient configuration through the autotune
-    cache (key: op, dtype, K, border, floor(log2(numel)))."""
+def _force_candidates(tmp_path, shape, K, border, dtype, choice):
+    """Pin configurations through the autotune cache: choice maps the tuner's
+    op index (0 forward, 1 input gradient, 2 filter gradient, 3 fused
+    backward) to a candidate id; key: op, dtype, K, border, floor(log2(numel))."""
     from paper_2504_01266_gb300 import _lib
     N, C, H, W = shape
     dt = _lib.GIGA_F32 if dtype == torch.float32 else _lib.GIGA_BF16
     b = BORDER[border]
     sc = int(math.floor(math.log2(N * C * H * W)))
-    path = tmp_path / f"tune_{cand}.json"
+    path = tmp_path / "tune.json"
     path.write_text(json.dumps({"giga_autotune": 1, "entries": {
-        f"{op}:{dt}:{K}:{b}:{sc}": cand for op in (0, 1)}}))
+        f"{op}:{dt}:{K}:{b}:{sc}": cand for op, cand in choice.items()}}))
     _lib.giga_autotune_clear()
     assert _lib.giga_autotune_load(str(path)) == _lib.GIGA_OK
     d = _lib.desc(N, C, C, H, W, K, C, b, dt, _lib.GIGA_LAYOUT_NCHW)
-    assert _lib.giga_autotune_choice(d, _lib.GIGA_OP_FWD) == cand
-    assert _lib.giga_autotune_choice(d, _lib.GIGA_OP_BWD_INPUT) == cand
+    ops = {0: _lib.GIGA_OP_FWD, 1: _lib.GIGA_OP_BWD_INPUT, 2: _lib.GIGA_OP_BWD_FILTER,
+           3: _lib.GIGA_OP_BWD_INPUT | _lib.GIGA_OP_BWD_FILTER}
+    for op, cand in choice.items():
+        assert _lib.giga_autotune_choice(d, ops[op]) == cand
 
 
-@pytest.mark.parametrize("K,border,dtype", [
-    (3, "zero", torch.float32), (3, "clamp", torch.float32), (15, "zero", torch.float32),
-    (15, "clamp", torch.float32), (3, "zero", torch.bfloat16), (15, "clamp", torch.bfloat16)])
-def test_fwd_every_configuration(giga, tmp_path, K, border, dtype):
+class _CachedMode:
+    def __enter__(self):
+        from paper_2504_01266_gb300 import _lib
+        self.mode = _lib.giga_autotune_get_mode()
+        _lib.giga_autotune_set_mode(1)
+
+    def __exit__(self, *exc):
+        from paper_2504_01266_gb300 import _lib
+        _lib.giga_autotune_clear()
+        _lib.giga_autotune_set_mode(self.mode)
+
+
+@pytest.mark.parametrize("K,border,dtype,W", [
+    (3, "zero", torch.float32, 1000), (3, "clamp", torch.float32, 998),
+    (15, "zero", torch.float32, 998), (15, "clamp", torch.float32, 1000),
+    (7, "clamp", torch.float32, 1000), (3, "zero", torch.bfloat16, 1000),
+    (15, "clamp", torch.bfloat16, 1000)])
+def test_fwd_every_configuration(giga, tmp_path, K, border, dtype, W):
     """Every forward / input-gradient configuration ({8, 4} rows per thread x
     one tile per CTA or persistent double-buffered CTAs) on planes holding
     more tiles than a persistent grid has CTAs, so each persistent CTA runs
     two or three tiles through its two shared-memory stages and the last
-    round is ragged; W = 998 also takes the scalar staging path."""
-    from paper_2504_01266_gb300 import _lib
-    shape = (4, 4, 520, 998 if dtype == torch.float32 else 1000)
+    round is ragged.  FP32 with W = 1000 is staged by TMA (the clamp border's
+    edge tiles then fixed in shared memory), W = 998 by cp.async."""
+    shape = (4, 4, 520, W)
     x, w, dy = make(shape, K, 600 + K, dtype)
     xc, wc, dyc = x.cuda(), w.cuda(), dy.cuda()
     b = BORDER[border]
@@ -176,11 +193,9 @@ def test_fwd_every_configuration(giga, tmp_path, K, border, dtype):
     if dtype == torch.float32:
         mag_y = oracle.dw_fwd(np.abs(xr), np.abs(wn), b)
         mag_dx = oracle.dw_bwd_input(np.abs(dyr), np.abs(wn), b)
-    mode = _lib.giga_autotune_get_mode()
-    _lib.giga_autotune_set_mode(1)
-    try:
+    with _CachedMode():
         for cand in range(4):
-            _force_fwd_candidate(tmp_path, shape, K, border, dtype, cand)
+            _force_candidates(tmp_path, shape, K, border, dtype, {0: cand, 1: cand})
             y = poison_like(xc)
             giga.conv2d_fwd(xc, wc, border, out=y)
             dx = poison_like(dyc)
@@ -193,9 +208,55 @@ def test_fwd_every_configuration(giga, tmp_path, K, border, dtype):
                 assert not torch.isnan(y).any() and not torch.isnan(dx).any(), what
                 assert normwise(to_np(y), ref_y) <= BF16_KERNEL_TOL, what
                 assert normwise(to_np(dx), ref_dx) <= BF16_KERNEL_TOL, what
-    finally:
-        _lib.giga_autotune_clear()
-        _lib.giga_autotune_set_mode(mode)
+
+
+@pytest.mark.parametrize("K,border,dtype,W", [
+    (3, "clamp", torch.float32, 1000), (9, "zero", torch.float32, 998),
+    (15, "clamp", torch.float32, 1000), (15, "zero", torch.float32, 1000),
+    (5, "clamp", torch.float32, 998), (7, "zero", torch.bfloat16, 1000),
+    (15, "clamp", torch.bfloat16, 1000)])
+def test_bwd_every_configuration(giga, tmp_path, K, border, dtype, W):
+    """Every filter-gradient configuration (tiles per chunk of the persistent
+    filter kernel) and every fused-backward configuration (the fused kernel
+    with each tiles-per-CTA choice, and the two-pass split) against the FP64
+    oracle.  16 planes of 520 x W hold 1152 tiles of 64 x 128: with 1 or 2
+    tiles per chunk every persistent CTA runs several chunks back to back,
+    so the shared-memory ring carries copies across chunk boundaries."""
+    shape = (4, 4, 520, 998)
+    x, w, dy = make(shape, K, 700 + K, dtype)
+    xc, wc, dyc = x.cuda(), w.cuda(), dy.cuda()
+    b = BORDER[border]
+    xr, dyr, wn = x.double().numpy(), dy.double().numpy(), w.numpy()
+    ref_dx = oracle.dw_bwd_input(dyr, wn, b)
+    ref_dw = oracle.dw_bwd_filter(xr, dyr, K, b)
+    mag_dx = oracle.dw_bwd_input(np.abs(dyr), np.abs(wn), b)
+    mag_dw = oracle.dw_bwd_filter(np.abs(xr), np.abs(dyr), K, b)
+    n = shape[0] * shape[2] * shape[3]
+    nan_dw = lambda: torch.full((shape[1], K, K), float("nan"), device="cuda")
+
+    def check_dw(dw, what):
+        if dtype == torch.float32:
+            assert_fp32(to_np(dw), ref_dw, mag_dw, n, what)
+        else:   # FP32 accumulation of the BF16 inputs (exact products)
+            assert normwise(to_np(dw), ref_dw) <= FP32_TOL, what
+
+    def check_dx(dx, what):
+        if dtype == torch.float32:
+            assert_fp32(to_np(dx), ref_dx, mag_dx, (K // 2 + 1) ** 2 * K * K, what)
+        else:
+            assert not torch.isnan(dx).any(), what
+            assert normwise(to_np(dx), ref_dx) <= BF16_KERNEL_TOL, what
+
+    with _CachedMode():
+        for cand in range(5):
+            _force_candidates(tmp_path, shape, K, border, dtype, {2: cand})
+            check_dw(giga.conv2d_bwd_filter(xc, dyc, K, border, out=nan_dw()),
+                     (K, border, dtype, "filter", cand))
+        for cand in range(6):
+            _force_candidates(tmp_path, shape, K, border, dtype, {3: cand})
+            dx, dw = giga.conv2d_bwd(xc, dyc, wc, border, dx=poison_like(dyc), dw=nan_dw())
+            check_dx(dx, (K, border, dtype, "fused", cand))
+            check_dw(dw, (K, border, dtype, "fused", cand))
 
 
 # ------------------------------------------------------- full-size workloads
