@@ -743,7 +743,7 @@ __global__ void __launch_bounds__(kThreads, bwd_min_ctas<T, K>())
 // ------------------------------------------------------- filter gradient
 // The filter gradient alone (Eq. 3's adjoint with respect to the filter):
 // dw[c][a][b] = sum over n, i, j of dy[n][c][i][j] * xs[n][c][i + a - r][j + b - r],
-// xs the border-extended input.  One CTA of 16 warps per SM, persistent over
+// xs the border-extended input.  One CTA of 12 or 16 warps per SM, persistent over
 // chunks of `tpc` consecutive 64 x 128 tiles of one plane (chunk q runs on
 // CTA q mod gridDim.x).  NS shared-memory stages hold {x tile with halo, dy
 // tile}; the copies of the tile NS - 1 items ahead are in flight while the
@@ -756,16 +756,24 @@ __global__ void __launch_bounds__(kThreads, bwd_min_ctas<T, K>())
 // holds one warp of every group.  At the end of a chunk the warps' sums
 // (fixed butterfly order) and then the group's warps (fixed order) give the
 // chunk's partial for every tap.
-constexpr int kFilterWarps = 16;
-constexpr int kFilterThreads = kFilterWarps * 32;
 constexpr int kFilterTileH = 64;
 static_assert(kFilterTileH == kBwdTileH, "both filter-gradient kernels share the chunk layout");
+
+// Warps and tap-row groups: K = 9 and 15 split into 3 equal groups (12 warps,
+// up to 170 registers for the larger accumulator set); the rest use 16 warps
+// and dw_groups<K>().
+template <int K>
+constexpr int filter_warps() {
+  return (K == 9 || K == 15) ? 12 : 16;
+}
 
 template <int K, typename T>
 struct FilterShape {
   using G = Geo<K>;
-  static constexpr int GT = dw_groups<K>();
-  static constexpr int WPG = kFilterWarps / GT;
+  static constexpr int NW = filter_warps<K>();
+  static constexpr int NT = NW * 32;
+  static constexpr int GT = NW == 12 ? 3 : dw_groups<K>();
+  static constexpr int WPG = NW / GT;
   static constexpr int AT = (K + GT - 1) / GT;
   static constexpr int ROWS = kFilterTileH / WPG;  // tile rows per warp
   static constexpr int DR = 4;                     // dy rows per unrolled block
@@ -776,14 +784,14 @@ struct FilterShape {
   static constexpr int STAGE_BYTES = round_up(DY_OFF + DY_BYTES, 128);
   static constexpr int NS = K <= 9 ? 3 : 2;
   static constexpr int SM_RED = NS * STAGE_BYTES;
-  static constexpr int SM_BAR = round_up(SM_RED + kFilterWarps * AT * K * 4, 8);
+  static constexpr int SM_BAR = round_up(SM_RED + NW * AT * K * 4, 8);
   static constexpr int SM_BYTES = SM_BAR + NS * 8 + 8;  // mbarriers, abort flag
-  static_assert(kFilterWarps % GT == 0 && ROWS % DR == 0, "warps own whole row blocks");
+  static_assert(NW % GT == 0 && NW % 4 == 0 && ROWS % DR == 0, "warps own whole row blocks");
   static_assert(SM_BYTES <= 227 * 1024, "shared memory");
 };
 
 template <typename T, int K>
-__global__ void __launch_bounds__(kFilterThreads, 1)
+__global__ void __launch_bounds__(FilterShape<K, T>::NT, 1)
     dw_filter_kernel(const __grid_constant__ CUtensorMap tmx,
                      const __grid_constant__ CUtensorMap tmdy, const T* __restrict__ x,
                      const T* __restrict__ dy, float* __restrict__ partials, int H, int W,
@@ -837,10 +845,10 @@ __global__ void __launch_bounds__(kFilterThreads, 1)
       }
     } else {
       const int64_t off = plane * (int64_t)H * W;
-      stage_tile<T, G::R, G::RP, G::SP, kFilterThreads, false>(sx, x + off, H, W, ty0, tx0,
-                                                               S::X_ROWS, clamp != 0, vec != 0);
-      stage_tile<T, 0, 0, kTileW, kFilterThreads, false>(sdy, dy + off, H, W, ty0, tx0,
-                                                         kFilterTileH, false, vec != 0);
+      stage_tile<T, G::R, G::RP, G::SP, S::NT, false>(sx, x + off, H, W, ty0, tx0, S::X_ROWS,
+                                                      clamp != 0, vec != 0);
+      stage_tile<T, 0, 0, kTileW, S::NT, false>(sdy, dy + off, H, W, ty0, tx0, kFilterTileH,
+                                                false, vec != 0);
     }
   };
 
@@ -897,7 +905,7 @@ __global__ void __launch_bounds__(kFilterThreads, 1)
     T* sx = reinterpret_cast<T*>(sm + sb * S::STAGE_BYTES);
     const T* sdy = reinterpret_cast<const T*>(sm + sb * S::STAGE_BYTES + S::DY_OFF);
     if (use_tma && clamp && at_edge(cs))
-      clamp_fix<T, G::SP, kFilterThreads>(sx, H, W, (cs.t / tiles_x) * kFilterTileH,
+      clamp_fix<T, G::SP, S::NT>(sx, H, W, (cs.t / tiles_x) * kFilterTileH,
                                           (cs.t % tiles_x) * kTileW, G::R, G::RP, S::X_ROWS);
     dw_rows<K, S::AT, S::GT, kTileW, S::DR, T>(sdy + part * S::ROWS * kTileW + 4 * lane,
                                                sx + (part * S::ROWS + a_lo) * G::SP + 4 * lane,
@@ -917,7 +925,7 @@ __global__ void __launch_bounds__(kFilterThreads, 1)
     }
     cta_barrier();  // stage sb is free again; sm_red is complete
     if (chunk_end) {
-      for (int k = threadIdx.x; k < K * K; k += kFilterThreads) {
+      for (int k = threadIdx.x; k < K * K; k += S::NT) {
         const int a = k / K, b = k - (k / K) * K;
         int gg = 0;
         while (gg + 1 < S::GT && group_lo(gg + 1, K, S::GT) <= a) ++gg;

@@ -119,7 +119,7 @@ static cudaError_t filter_impl(const DwArgs& a, const DwConfig& cfg, cudaStream_
   int& per_sm = ctas_per_sm[dev & 63];
   if (per_sm == 0) {
     int v = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kern, kFilterThreads, smem) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kern, S::NT, smem) !=
             cudaSuccess ||
         v < 1)
       v = 1;
@@ -141,7 +141,7 @@ static cudaError_t filter_impl(const DwArgs& a, const DwConfig& cfg, cudaStream_
               make_plane_map_f32(&tmdy, a.dy, a.W, a.H, a.N * a.C, kTileW, kFilterTileH);
   }
   int* err = dw_error_word();
-  kern<<<(unsigned)grid, kFilterThreads, smem, st>>>(
+  kern<<<(unsigned)grid, S::NT, smem, st>>>(
       tmx, tmdy, static_cast<const T*>(a.x), static_cast<const T*>(a.dy), a.partials, (int)a.H,
       (int)a.W, (int)tiles_x, (int)(tiles_x * tiles_y), (int)chunks, cfg.tiles_per_cta,
       num_chunks, a.border, a.vec, use_tma, err);
