@@ -34,13 +34,19 @@
 
 namespace giga {
 
-template <int K>
+// Tile geometry of a K x K filter for elements of ES bytes.
+template <int K, int ES = 4>
 struct Geo {
   static constexpr int R = (K - 1) / 2;
-  static constexpr int RP = (R + 3) / 4 * 4;        // column halo rounded up to 4
+  // column halo rounded up to 16 bytes of elements (4 FP32, 8 BF16), so a
+  // staged row starts 16-byte aligned in memory (TMA's rule for the x
+  // coordinate) and in shared memory
+  static constexpr int RP = ES == 2 ? (R + 7) / 8 * 8 : (R + 3) / 4 * 4;
   static constexpr int SP = kTileW + 2 * RP;        // staged row pitch (elements)
   static constexpr int OFF = RP - R;                // first column a lane needs
-  static constexpr int NV = (OFF + K + 2) / 4 + 1;  // float4 loads per lane per row
+  static constexpr int OFF4 = OFF / 4 * 4;          // whole 4-element chunks skipped
+  static constexpr int OFFR = OFF - OFF4;           // offset inside the first chunk
+  static constexpr int NV = (OFFR + K + 2) / 4 + 1;  // 4-element loads per lane per row
   static constexpr int KP = (K + 3) / 4 * 4;         // staged filter row pitch
   static constexpr int WPAD = K * KP;               // staged filter (floats)
 };
@@ -99,7 +105,7 @@ __device__ __forceinline__ void stage_wait() {
 // in registers (used for filter taps and dy blocks that feed many FMAs).
 __device__ __forceinline__ float4 lds128_pinned(const float* p) {
   float4 v;
-  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+  asm volatile("ld.volatile.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
                : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
                : "r"(smem_addr(p)));
   return v;
@@ -127,7 +133,8 @@ template <> struct Tile<__nv_bfloat16> {
   }
   static __device__ __forceinline__ float4 load4_pinned(const __nv_bfloat16* p) {
     uint32_t lo, hi;
-    asm volatile("ld.shared.v2.b32 {%0, %1}, [%2];" : "=r"(lo), "=r"(hi) : "r"(smem_addr(p)));
+    asm volatile("ld.volatile.shared.v2.b32 {%0, %1}, [%2];" : "=r"(lo), "=r"(hi)
+                 : "r"(smem_addr(p)));
     return bf16x4_to_float4(lo, hi);
   }
   // values come from BF16 storage, so the round trip is exact
@@ -316,12 +323,15 @@ __device__ __forceinline__ void store_block(T* __restrict__ plane, int H, int W,
   }
 }
 
+// The window of a lane's 4 output columns: staged columns from the lane's
+// first column + OFF4 on (buf[OFFR + px + b] is input column px + b - r).
 template <int K, typename TS>
 __device__ __forceinline__ void load_window_row(const TS* __restrict__ row,
-                                                float (&buf)[4 * Geo<K>::NV]) {
+                                                float (&buf)[4 * Geo<K, sizeof(TS)>::NV]) {
+  using G = Geo<K, sizeof(TS)>;
 #pragma unroll
-  for (int v = 0; v < Geo<K>::NV; ++v) {
-    const float4 t = Tile<TS>::load4(row + 4 * v);
+  for (int v = 0; v < G::NV; ++v) {
+    const float4 t = Tile<TS>::load4(row + G::OFF4 + 4 * v);
     buf[4 * v + 0] = t.x;
     buf[4 * v + 1] = t.y;
     buf[4 * v + 2] = t.z;
@@ -335,7 +345,7 @@ __device__ __forceinline__ void load_window_row(const TS* __restrict__ row,
 template <int K, int PY, int A, typename TS>
 __device__ __forceinline__ void fwd_group(const TS* __restrict__ win,
                                           const float* __restrict__ f, float (&acc)[PY][4]) {
-  using G = Geo<K>;
+  using G = Geo<K, sizeof(TS)>;
   float wr[A][G::KP];
 #pragma unroll
   for (int s = 0; s < A; ++s)
@@ -359,7 +369,7 @@ __device__ __forceinline__ void fwd_group(const TS* __restrict__ win,
         for (int b = 0; b < K; ++b)
 #pragma unroll
           for (int px = 0; px < 4; ++px)
-            acc[py][px] = fmaf(wr[s][b], buf[G::OFF + px + b], acc[py][px]);
+            acc[py][px] = fmaf(wr[s][b], buf[G::OFFR + px + b], acc[py][px]);
       }
     }
   }
@@ -377,9 +387,9 @@ __device__ __forceinline__ void fwd_block(const TS* __restrict__ win,
     for (int px = 0; px < 4; ++px) acc[py][px] = 0.f;
 #pragma unroll 1
   for (int g = 0; g < NG; ++g)
-    fwd_group<K, PY, A, TS>(win + g * A * Geo<K>::SP, f + g * A * Geo<K>::KP, acc);
+    fwd_group<K, PY, A, TS>(win + g * A * Geo<K, sizeof(TS)>::SP, f + g * A * Geo<K>::KP, acc);
   if constexpr (REM > 0)
-    fwd_group<K, PY, REM, TS>(win + NG * A * Geo<K>::SP, f + NG * A * Geo<K>::KP, acc);
+    fwd_group<K, PY, REM, TS>(win + NG * A * Geo<K, sizeof(TS)>::SP, f + NG * A * Geo<K>::KP, acc);
 }
 
 // Filter gradient of one DR-row dy block for the NR filter rows [a_lo, a_lo + NR):
@@ -393,7 +403,7 @@ template <int K, int NR, int AT, int DYP, int DR, typename TS>
 __device__ __forceinline__ void dw_block(const TS* __restrict__ dyb,
                                          const TS* __restrict__ xw, float (&acc)[AT][K]) {
   static_assert(NR >= 1 && NR <= AT, "row count");
-  using G = Geo<K>;
+  using G = Geo<K, sizeof(TS)>;
   float d[DR][4];
 #pragma unroll
   for (int py = 0; py < DR; ++py) {
@@ -415,7 +425,7 @@ __device__ __forceinline__ void dw_block(const TS* __restrict__ dyb,
         for (int b = 0; b < K; ++b)
 #pragma unroll
           for (int px = 0; px < 4; ++px)
-            acc[s][b] = fmaf(d[py][px], buf[G::OFF + px + b], acc[s][b]);
+            acc[s][b] = fmaf(d[py][px], buf[G::OFFR + px + b], acc[s][b]);
       }
     }
   }
@@ -428,7 +438,7 @@ __device__ __forceinline__ void dw_block(const TS* __restrict__ dyb,
 template <int K, int AT, int GT, int DYP, int DR, typename TS>
 __device__ __forceinline__ void dw_rows(const TS* __restrict__ dyb, const TS* __restrict__ xw,
                                         int nblocks, int nrows, float (&acc)[AT][K]) {
-  constexpr int SP = Geo<K>::SP;
+  constexpr int SP = Geo<K, sizeof(TS)>::SP;
   if constexpr (K % GT == 0) {
 #pragma unroll 1
     for (int i = 0; i < nblocks; ++i)
@@ -466,7 +476,7 @@ constexpr int round_up(int v, int m) { return (v + m - 1) / m * m; }
 
 template <int K, int PY, typename T>
 struct FwdShape {
-  using G = Geo<K>;
+  using G = Geo<K, sizeof(T)>;
   static constexpr int TH = kWarps * PY;
   static constexpr int ROWS = TH + 2 * G::R;
   static constexpr int TILE_BYTES = ROWS * G::SP * (int)sizeof(T);
@@ -482,7 +492,7 @@ __global__ void __launch_bounds__(kThreads) dw_fwd_kernel(
     const __grid_constant__ CUtensorMap tmx, const T* __restrict__ x, const float* __restrict__ w,
     T* __restrict__ y, int C, int H, int W, int tiles_x, int tiles_y, int64_t num_tiles, int clamp,
     int vec, int flip, int use_tma, int* err) {
-  using G = Geo<K>;
+  using G = Geo<K, sizeof(T)>;
   using S = FwdShape<K, PY, T>;
   constexpr int TH = S::TH;
   extern __shared__ __align__(128) float smem[];
@@ -575,7 +585,7 @@ __global__ void __launch_bounds__(kThreads) dw_fwd_kernel(
 // cp.async with the border applied.
 template <int K, typename T>
 struct BwdShape {
-  using G = Geo<K>;
+  using G = Geo<K, sizeof(T)>;
   static constexpr int NDX = 4;
   static constexpr int NDW = kWarps - NDX;
   static constexpr int GT = dw_groups<K>();
@@ -613,7 +623,7 @@ __global__ void __launch_bounds__(kThreads, bwd_min_ctas<T, K>())
                   float* __restrict__ partials, int C, int H, int W, int tiles_x,
                   int tiles_per_plane, int chunks_per_plane, int tpc, int clamp, int vec,
                   int use_tma, int* err) {
-  using G = Geo<K>;
+  using G = Geo<K, sizeof(T)>;
   using S = BwdShape<K, T>;
   extern __shared__ __align__(128) float smem[];
   char* sm = reinterpret_cast<char*>(smem);
@@ -769,7 +779,7 @@ constexpr int filter_warps() {
 
 template <int K, typename T>
 struct FilterShape {
-  using G = Geo<K>;
+  using G = Geo<K, sizeof(T)>;
   static constexpr int NW = filter_warps<K>();
   static constexpr int NT = NW * 32;
   static constexpr int GT = NW == 12 ? 3 : dw_groups<K>();
@@ -797,7 +807,7 @@ __global__ void __launch_bounds__(FilterShape<K, T>::NT, 1)
                      const T* __restrict__ dy, float* __restrict__ partials, int H, int W,
                      int tiles_x, int tiles_per_plane, int chunks_per_plane, int tpc,
                      int64_t num_chunks, int clamp, int vec, int use_tma, int* err) {
-  using G = Geo<K>;
+  using G = Geo<K, sizeof(T)>;
   using S = FilterShape<K, T>;
   extern __shared__ __align__(128) float smem[];
   char* sm = reinterpret_cast<char*>(smem);

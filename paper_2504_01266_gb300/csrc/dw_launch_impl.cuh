@@ -44,12 +44,13 @@ static cudaError_t fwd_impl(const DwArgs& a, bool input_grad, bool persistent, c
   if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
   const T* in = static_cast<const T*>(input_grad ? a.dy : a.x);
   T* out = static_cast<T*>(input_grad ? a.dx : a.y);
-  // TMA staging for FP32 rows with a 16-byte stride from a 16-byte aligned base
+  // TMA staging for rows with a 16-byte stride from a 16-byte aligned base
   CUtensorMap tm;
   std::memset(&tm, 0, sizeof(tm));
   int use_tma = 0;
-  if (sizeof(T) == 4 && a.vec)
-    use_tma = make_plane_map_f32(&tm, in, a.W, a.H, a.N * a.C, Geo<K>::SP, S::ROWS);
+  if (plane_tma_ok(in, sizeof(T), a.W))
+    use_tma = make_plane_map(&tm, in, sizeof(T), a.W, a.H, a.N * a.C, Geo<K, sizeof(T)>::SP,
+                             S::ROWS);
   kern<<<(unsigned)grid, kThreads, smem, st>>>(tm, in, a.w, out, (int)a.C, (int)a.H, (int)a.W,
                                                (int)tiles_x, (int)tiles_y, tiles,
                                                input_grad ? 0 : a.border, a.vec,
@@ -86,9 +87,10 @@ static cudaError_t bwd_impl(const DwArgs& a, const DwConfig& cfg, cudaStream_t s
   std::memset(&tmx, 0, sizeof(tmx));
   std::memset(&tmdy, 0, sizeof(tmdy));
   int use_tma = 0;
-  if (sizeof(T) == 4 && a.vec)
-    use_tma = make_plane_map_f32(&tmx, a.x, a.W, a.H, a.N * a.C, Geo<K>::SP, S::ROWS) &&
-              make_plane_map_f32(&tmdy, a.dy, a.W, a.H, a.N * a.C, Geo<K>::SP, S::ROWS);
+  constexpr int es = sizeof(T);
+  if (plane_tma_ok(a.x, es, a.W) && plane_tma_ok(a.dy, es, a.W))
+    use_tma = make_plane_map(&tmx, a.x, es, a.W, a.H, a.N * a.C, Geo<K, es>::SP, S::ROWS) &&
+              make_plane_map(&tmdy, a.dy, es, a.W, a.H, a.N * a.C, Geo<K, es>::SP, S::ROWS);
   kern<<<(unsigned)grid, kThreads, smem, st>>>(
       tmx, tmdy, static_cast<const T*>(a.x), static_cast<const T*>(a.dy), a.w,
       static_cast<T*>(a.dx), a.partials, (int)a.C, (int)a.H, (int)a.W, (int)tiles_x, (int)tpp,
@@ -130,15 +132,16 @@ static cudaError_t filter_impl(const DwArgs& a, const DwConfig& cfg, cudaStream_
   const int64_t chunks = dw_bwd_chunks_per_plane(a.H, a.W, cfg.tiles_per_cta);
   const int64_t num_chunks = a.N * a.C * chunks;
   const int64_t grid = std::min<int64_t>(num_chunks, (int64_t)per_sm * sm_count());
-  // TMA staging: FP32 rows with a 16-byte stride from 16-byte aligned bases
-  // (the vectorised-access condition); otherwise cp.async staging.
+  // TMA staging: rows with a 16-byte stride from 16-byte aligned bases;
+  // otherwise cp.async staging.
   CUtensorMap tmx, tmdy;
   std::memset(&tmx, 0, sizeof(tmx));
   std::memset(&tmdy, 0, sizeof(tmdy));
   int use_tma = 0;
-  if (sizeof(T) == 4 && a.vec) {
-    use_tma = make_plane_map_f32(&tmx, a.x, a.W, a.H, a.N * a.C, Geo<K>::SP, S::X_ROWS) &&
-              make_plane_map_f32(&tmdy, a.dy, a.W, a.H, a.N * a.C, kTileW, kFilterTileH);
+  constexpr int es = sizeof(T);
+  if (plane_tma_ok(a.x, es, a.W) && plane_tma_ok(a.dy, es, a.W)) {
+    use_tma = make_plane_map(&tmx, a.x, es, a.W, a.H, a.N * a.C, Geo<K, es>::SP, S::X_ROWS) &&
+              make_plane_map(&tmdy, a.dy, es, a.W, a.H, a.N * a.C, kTileW, kFilterTileH);
   }
   int* err = dw_error_word();
   kern<<<(unsigned)grid, S::NT, smem, st>>>(

@@ -55,7 +55,7 @@ struct RagParams {
 
 template <int K, typename T>
 struct RagShape {
-  using G = Geo<K>;
+  using G = Geo<K, sizeof(T)>;
   static constexpr int GT = dw_groups<K>();
   static constexpr int WPG = 4 / GT;
   static constexpr int AT = (K + GT - 1) / GT;
@@ -78,7 +78,7 @@ constexpr size_t rag_max_smem() {
 template <typename T, int K>
 __device__ __forceinline__ void rag_chunk(const RagParams& p, const RagChunk& ch,
                                           const RagImage& im, float* smem, int* s_flag) {
-  using G = Geo<K>;
+  using G = Geo<K, sizeof(T)>;
   using S = RagShape<K, T>;
   constexpr int KK = K * K;
   char* sm = reinterpret_cast<char*>(smem);

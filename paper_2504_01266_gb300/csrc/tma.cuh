@@ -142,20 +142,27 @@ inline EncodeFn encode_fn() {
   return fn;
 }
 
-// A stack of `planes` row-major H x W FP32 planes as a 3-D tensor (x fastest)
-// with a box of bw x bh x 1; loads outside the tensor read zeros.  Requires a
-// 16-byte aligned base and W % 4 == 0 (16-byte row stride).
-inline bool make_plane_map_f32(CUtensorMap* m, const void* base, int64_t W, int64_t H,
-                               int64_t planes, int bw, int bh) {
+// A stack of `planes` row-major H x W planes (FP32 if es == 4, BF16 if
+// es == 2) as a 3-D tensor (x fastest) with a box of bw x bh x 1; loads
+// outside the tensor read zeros.  Requires a 16-byte aligned base and a row
+// stride W * es that is a multiple of 16 bytes (see plane_tma_ok).
+inline bool make_plane_map(CUtensorMap* m, const void* base, int es, int64_t W, int64_t H,
+                           int64_t planes, int bw, int bh) {
   EncodeFn enc = encode_fn();
   if (!enc) return false;
   cuuint64_t dims[3] = {(cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)planes};
-  cuuint64_t strides[2] = {(cuuint64_t)W * 4, (cuuint64_t)(H * W) * 4};
+  cuuint64_t strides[2] = {(cuuint64_t)(W * es), (cuuint64_t)(H * W * es)};
   cuuint32_t box[3] = {(cuuint32_t)bw, (cuuint32_t)bh, 1};
   cuuint32_t estr[3] = {1, 1, 1};
-  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(base), dims, strides, box,
-             estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  return enc(m, es == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+             const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Planes at `base` can be staged by TMA: 16-byte aligned base and row stride.
+inline bool plane_tma_ok(const void* base, int es, int64_t W) {
+  return base && (reinterpret_cast<uintptr_t>(base) % 16) == 0 && (W * es) % 16 == 0;
 }
 
 }  // namespace giga

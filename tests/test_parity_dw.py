@@ -93,8 +93,10 @@ def test_bwd_fused_and_filter_fp32(giga, K, border):
 
 @pytest.mark.parametrize("K", [3, 9, 15])
 @pytest.mark.parametrize("border", ["zero", "clamp"])
-def test_bf16(giga, K, border):
-    shape = (2, 3, 67, 260)
+@pytest.mark.parametrize("shape", [(2, 3, 67, 260), (1, 2, 130, 264)])
+def test_bf16(giga, K, border, shape):
+    """BF16 storage: W = 260 rows (520 bytes) are staged by cp.async, W = 264
+    rows (528 bytes, 16-byte multiple) by TMA."""
     x32, w, dy32 = make(shape, K, 400 + K)
     xb, dyb = x32.to(torch.bfloat16), dy32.to(torch.bfloat16)
     y = giga.conv2d_fwd(xb.cuda(), w.cuda(), border)
