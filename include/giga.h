@@ -206,11 +206,19 @@ void giga_autotune_clear(void);
 
 /* ------------------------------------------------------------------------ */
 const char* giga_status_string(giga_status_t status);
-/* Synchronise `stream`, then read and clear the device error word that the
- * pipelined tensor-core kernels set when a bounded wait on one of their
- * barriers expires (they then stop issuing work and release their tensor
- * memory instead of hanging).  Returns GIGA_ERR_TIMEOUT if it was set. */
+/* Synchronise `stream`, then read and clear the device error words that the
+ * kernels set when a bounded wait expires: the pipelined tensor-core kernels
+ * (a barrier of their TMA / MMA pipeline) and the depthwise kernels (a TMA
+ * tile load).  Such a kernel then stops issuing work, lets copies already in
+ * flight land, releases its tensor memory and returns instead of hanging.
+ * Returns GIGA_ERR_TIMEOUT if either word was set. */
 giga_status_t giga_check_device_error(void* stream);
+/* Failure-path self-test: launch one thread that waits on a barrier nothing
+ * completes; its bounded wait gives up after 2 s and sets the depthwise error
+ * word, so the next giga_check_device_error on the same stream returns
+ * GIGA_ERR_TIMEOUT (and clears it).  Asynchronous; the device stays usable.
+ * Not part of the paper's method: it exists to test failure detection. */
+giga_status_t giga_selftest_bounded_wait(void* stream);
 /* Description of the last error on the calling thread ("" if none). */
 const char* giga_last_error_detail(void);
 /* Kernel launches issued by this library on the calling thread since the last

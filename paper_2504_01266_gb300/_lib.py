@@ -42,7 +42,8 @@ EXPORTS = (
     "giga_batched_plan_destroy", "giga_conv2d_batched", "giga_conv2d_batched_workspace_size",
     "giga_autotune_set_mode", "giga_autotune_get_mode", "giga_autotune_conv2d",
     "giga_autotune_choice", "giga_autotune_save", "giga_autotune_load", "giga_autotune_clear",
-    "giga_status_string", "giga_check_device_error", "giga_last_error_detail",
+    "giga_status_string", "giga_check_device_error", "giga_selftest_bounded_wait",
+    "giga_last_error_detail",
     "giga_launch_count",
     "giga_launch_count_reset",
 )
@@ -102,6 +103,7 @@ _SIGS = {
     "giga_autotune_clear": (None, []),
     "giga_status_string": (ctypes.c_char_p, [_ST]),
     "giga_check_device_error": (_ST, [_P]),
+    "giga_selftest_bounded_wait": (_ST, [_P]),
     "giga_last_error_detail": (ctypes.c_char_p, []),
     "giga_launch_count": (ctypes.c_uint64, []),
     "giga_launch_count_reset": (None, []),
@@ -243,6 +245,10 @@ def giga_autotune_clear() -> None:
 
 def giga_check_device_error(stream) -> int:
     return load().giga_check_device_error(stream)
+
+
+def giga_selftest_bounded_wait(stream) -> int:
+    return load().giga_selftest_bounded_wait(stream)
 
 
 def giga_launch_count() -> int:

@@ -479,6 +479,12 @@ giga_status_t giga_check_device_error(void* stream) {
   return GIGA_OK;
 }
 
+giga_status_t giga_selftest_bounded_wait(void* stream) {
+  clear_error();
+  cudaError_t e = dw_wait_selftest(static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? GIGA_OK : cuda_fail(e, "bounded-wait self-test launch");
+}
+
 uint64_t giga_launch_count(void) { return t_launches; }
 
 void giga_launch_count_reset(void) { t_launches = 0; }

@@ -33,6 +33,8 @@ cudaError_t dw_filter_launch(const DwArgs& a, const DwConfig& cfg, cudaStream_t 
 int* dw_error_word();
 // Synchronise `st`, read and clear that word.
 cudaError_t dw_take_error(cudaStream_t st, int* code);
+// Launch a kernel whose bounded mbarrier wait runs out (sets that word).
+cudaError_t dw_wait_selftest(cudaStream_t st);
 
 // Number of tile chunks per plane the backward pass uses for `tiles_per_cta`.
 int64_t dw_bwd_chunks_per_plane(int64_t H, int64_t W, int tiles_per_cta);

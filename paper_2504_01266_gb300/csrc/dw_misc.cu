@@ -6,6 +6,7 @@
 #include "dw_fold.cuh"
 #include "dw_kernels.cuh"
 #include "dw_launch.h"
+#include "tma.cuh"
 
 namespace giga {
 
@@ -34,6 +35,25 @@ cudaError_t dw_take_error(cudaStream_t st, int* code) {
   if (e != cudaSuccess) return e;
   const int zero = 0;
   return cudaMemcpy(err, &zero, sizeof(int), cudaMemcpyHostToDevice);
+}
+
+// One thread waits on an mbarrier that nothing ever completes: the bounded
+// wait gives up after kWaitLimitNs and records kDevErrTimeout, exercising the
+// same path a stalled TMA load would take.
+__global__ void dw_wait_selftest_kernel(int* err) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x != 0) return;
+  mbar_init(&bar, 1);
+  mbar_init_fence();
+  if (!mbar_wait(&bar, 0)) record_error(err, kDevErrTimeout);
+}
+
+cudaError_t dw_wait_selftest(cudaStream_t st) {
+  int* err = dw_error_word();
+  if (!err) return cudaErrorInvalidSymbol;
+  dw_wait_selftest_kernel<<<1, 32, 0, st>>>(err);
+  note_launch();
+  return cudaGetLastError();
 }
 
 int64_t dw_bwd_chunks_per_plane(int64_t H, int64_t W, int tiles_per_cta) {
