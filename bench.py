@@ -296,6 +296,33 @@ def compare_bf16(dev, iters):
     out["bf16"]["err_normwise_sampled"] = errs["bf16"]
     out["bf16_over_fp32"] = out["bf16"]["value"] / out["fp32"]["value"]
     out["workload"] = "32x3x2048x2048, K=9 normal(0,0.1), zero border, fwd+bwd"
+    # K = 9 is past the FP32 ridge (both storage types are ALU-bound); the same
+    # images with a 3 x 3 filter are HBM-bound, where halving the bytes pays.
+    del res
+    k3 = {}
+    w3 = (torch.randn((Cb, 3, 3), generator=torch.Generator().manual_seed(2509)) * 0.1).to(dev)
+    for name, dt in (("fp32", torch.float32), ("bf16", torch.bfloat16)):
+        x, dy = x32.to(dt), dy32.to(dt)
+        y, dx = torch.empty_like(x), torch.empty_like(x)
+        dw = torch.empty((Cb, 3, 3), device=dev)
+        d = L.desc(Nb, Cb, Cb, Hb, Wb, 3, Cb, 0, L.GIGA_F32 if dt == torch.float32 else L.GIGA_BF16,
+                   L.GIGA_LAYOUT_NCHW)
+        wsb = L.giga_conv2d_workspace_size(d, 6)
+        ws = torch.empty(wsb, dtype=torch.uint8, device=dev)
+        L.check(L.giga_autotune_conv2d(d, 7, x.data_ptr(), w3.data_ptr(), y.data_ptr(),
+                                       dy.data_ptr(), dx.data_ptr(), dw.data_ptr(), ws.data_ptr(),
+                                       wsb, sp), "autotune")
+
+        def run3():
+            L.check(L.giga_conv2d_fwd(d, x.data_ptr(), w3.data_ptr(), y.data_ptr(), None, 0, sp),
+                    "fwd")
+            L.check(L.giga_conv2d_bwd(d, x.data_ptr(), dy.data_ptr(), w3.data_ptr(), dx.data_ptr(),
+                                      dw.data_ptr(), ws.data_ptr(), wsb, sp), "bwd")
+        k3[name + "_ms"] = _events(stream, run3, iters)
+        del x, dy, y, dx, ws
+    k3["bf16_over_fp32"] = k3["fp32_ms"] / k3["bf16_ms"]
+    k3["workload"] = "32x3x2048x2048, K=3 normal(0,0.1), zero border, fwd+bwd (HBM-bound)"
+    out["k3"] = k3
     return out
 
 

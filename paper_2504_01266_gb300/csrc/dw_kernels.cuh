@@ -51,6 +51,8 @@ struct Geo {
   static constexpr int WPAD = K * KP;               // staged filter (floats)
 };
 
+constexpr int round_up(int v, int m) { return (v + m - 1) / m * m; }
+
 // Filter rows held in registers per pass of the forward-style loop.
 template <int K>
 constexpr int fwd_group_rows() {
@@ -239,6 +241,70 @@ __device__ __forceinline__ void stage_tile(T* __restrict__ sm, const T* __restri
     }
   }
   if (COMMIT) cp_async_commit();
+}
+
+// Staged-tile layout of storage type T in a buffer sized for the FP32 tile of
+// ROWS x SPD elements: FP32 tiles are staged in place; a BF16 tile of ROWS x
+// SPS elements is staged at the end of the buffer (128-byte aligned for TMA)
+// and widened into the FP32 layout at the start by widen_tile, so every
+// compute path reads FP32 tiles.
+template <typename T, int ROWS, int SPD, int SPS>
+struct StagedTile {
+  static constexpr int BYTES = round_up(ROWS * SPD * 4, 128);  // the FP32 tile
+  static constexpr int STAGE_BYTES = ROWS * SPS * (int)sizeof(T);
+  static constexpr int STAGE_OFF = sizeof(T) == 4 ? 0 : (BYTES - STAGE_BYTES) / 128 * 128;
+  static_assert(sizeof(T) == 2 || SPS == SPD, "FP32 tiles are staged in their own layout");
+  static_assert(STAGE_OFF >= 0 && STAGE_OFF + STAGE_BYTES <= BYTES, "staged tile fits");
+};
+
+// Widen the BF16 tile staged at `src` (ROWS x SPS) into the FP32 tile at `dst`
+// (ROWS x SPD; FP32 column c is staged column c + D).  src lies at the end of
+// dst's buffer.  Chunks of 4 elements go in increasing order, PB per thread
+// per pass: a pass reads its chunks into registers, the CTA synchronises, then
+// it writes.  The FP32 writes of a pass never reach the staged bytes of a
+// later pass (the FP32 image of chunk k ends below the staged image of every
+// chunk after the pass, checked on the host for every shape in use), so only
+// the barrier between a pass's reads and writes is needed; a final barrier
+// publishes the FP32 tile.
+template <int ROWS, int SPD, int SPS, int D, int NT>
+__device__ __forceinline__ void widen_tile(float* __restrict__ dst,
+                                           const __nv_bfloat16* __restrict__ src) {
+  constexpr int CPR = SPD / 4;
+  constexpr int TOTAL = ROWS * CPR;
+  constexpr int PB = 4;
+  constexpr int PASSES = (TOTAL + NT * PB - 1) / (NT * PB);
+  static_assert(D % 4 == 0 && SPD % 4 == 0 && D + SPD <= SPS, "chunks stay aligned");
+#pragma unroll 1
+  for (int p = 0; p < PASSES; ++p) {
+    uint2 v[PB];
+#pragma unroll
+    for (int i = 0; i < PB; ++i) {
+      const int k = (p * PB + i) * NT + threadIdx.x;
+      if (k < TOTAL) {
+        const int r = k / CPR, c = (k - (k / CPR) * CPR) * 4;
+        v[i] = *reinterpret_cast<const uint2*>(src + r * SPS + c + D);
+      }
+    }
+    cta_barrier();
+#pragma unroll
+    for (int i = 0; i < PB; ++i) {
+      const int k = (p * PB + i) * NT + threadIdx.x;
+      if (k < TOTAL) {
+        const int r = k / CPR, c = (k - (k / CPR) * CPR) * 4;
+        *reinterpret_cast<float4*>(dst + r * SPD + c) = bf16x4_to_float4(v[i].x, v[i].y);
+      }
+    }
+  }
+  cta_barrier();
+}
+
+// The halo tile of filter size K (ROWS rows) staged as T, widened if BF16.
+template <int K, typename T, int ROWS>
+using HaloTile = StagedTile<T, ROWS, Geo<K, 4>::SP, Geo<K, sizeof(T)>::SP>;
+
+template <int K, int ROWS, int NT>
+__device__ __forceinline__ void widen_halo_tile(float* dst, const __nv_bfloat16* src) {
+  widen_tile<ROWS, Geo<K, 4>::SP, Geo<K, 2>::SP, Geo<K, 2>::RP - Geo<K, 4>::RP, NT>(dst, src);
 }
 
 // Clamp border on a tile that TMA staged with zeros outside the image: tile
@@ -472,15 +538,13 @@ constexpr int bwd_block_rows() {
 // shared memory: while a tile is computed, the cp.async copies of the next
 // tile and of its plane's filter are in flight.  With flip = 1 the filter is
 // rotated by 180 degrees: that computes g (input gradient, zero border) from dy.
-constexpr int round_up(int v, int m) { return (v + m - 1) / m * m; }
-
 template <int K, int PY, typename T>
 struct FwdShape {
-  using G = Geo<K, sizeof(T)>;
+  using G = Geo<K>;  // FP32 compute geometry
   static constexpr int TH = kWarps * PY;
   static constexpr int ROWS = TH + 2 * G::R;
-  static constexpr int TILE_BYTES = ROWS * G::SP * (int)sizeof(T);
-  static constexpr int W_OFF = round_up(TILE_BYTES, 16);  // tile (TMA: 128-aligned), then filter
+  using ST = HaloTile<K, T, ROWS>;
+  static constexpr int W_OFF = ST::BYTES;  // FP32 tile (128-aligned), then the filter
   static constexpr int STAGE_BYTES = round_up(W_OFF + G::WPAD * 4, 128);
   static constexpr int HEAD = 128;  // two mbarriers and the abort flag
   static constexpr int SM_BYTES = HEAD + 2 * STAGE_BYTES;
@@ -492,8 +556,10 @@ __global__ void __launch_bounds__(kThreads) dw_fwd_kernel(
     const __grid_constant__ CUtensorMap tmx, const T* __restrict__ x, const float* __restrict__ w,
     T* __restrict__ y, int C, int H, int W, int tiles_x, int tiles_y, int64_t num_tiles, int clamp,
     int vec, int flip, int use_tma, int* err) {
-  using G = Geo<K, sizeof(T)>;
+  using G = Geo<K>;
+  using GS = Geo<K, sizeof(T)>;
   using S = FwdShape<K, PY, T>;
+  using ST = typename S::ST;
   constexpr int TH = S::TH;
   extern __shared__ __align__(128) float smem[];
   char* sm = reinterpret_cast<char*>(smem);
@@ -511,19 +577,20 @@ __global__ void __launch_bounds__(kThreads) dw_fwd_kernel(
     int ty0, tx0;
     int64_t plane;
     coords(t, ty0, tx0, plane);
-    T* sx = reinterpret_cast<T*>(sm + S::HEAD + sb * S::STAGE_BYTES);
-    float* sw = reinterpret_cast<float*>(sm + S::HEAD + sb * S::STAGE_BYTES + S::W_OFF);
+    char* buf = sm + S::HEAD + sb * S::STAGE_BYTES;
+    T* staged = reinterpret_cast<T*>(buf + ST::STAGE_OFF);
+    float* sw = reinterpret_cast<float*>(buf + S::W_OFF);
     stage_filter_async<K>(sw, w + (int64_t)(plane % C) * K * K, flip != 0, kThreads);
     if (use_tma) {
       cp_async_commit();
       if (threadIdx.x == 0) {
         fence_proxy_async();
-        mbar_expect_tx(bars + sb, (uint32_t)S::TILE_BYTES);
-        tma_load_3d(sx, &tmx, tx0 - G::RP, ty0 - G::R, (int)plane, bars + sb);
+        mbar_expect_tx(bars + sb, (uint32_t)ST::STAGE_BYTES);
+        tma_load_3d(staged, &tmx, tx0 - GS::RP, ty0 - G::R, (int)plane, bars + sb);
       }
     } else {
-      stage_tile<T, G::R, G::RP, G::SP>(sx, x + plane * (int64_t)H * W, H, W, ty0, tx0, S::ROWS,
-                                        clamp != 0, vec != 0);
+      stage_tile<T, G::R, GS::RP, GS::SP>(staged, x + plane * (int64_t)H * W, H, W, ty0, tx0,
+                                          S::ROWS, clamp != 0, vec != 0);
     }
   };
 
@@ -559,20 +626,25 @@ __global__ void __launch_bounds__(kThreads) dw_fwd_kernel(
     int ty0, tx0;
     int64_t plane;
     coords(t, ty0, tx0, plane);
-    T* sx = reinterpret_cast<T*>(sm + S::HEAD + sb * S::STAGE_BYTES);
-    const float* sw = reinterpret_cast<const float*>(sm + S::HEAD + sb * S::STAGE_BYTES + S::W_OFF);
+    char* buf = sm + S::HEAD + sb * S::STAGE_BYTES;
+    float* sx = reinterpret_cast<float*>(buf);
+    const float* sw = reinterpret_cast<const float*>(buf + S::W_OFF);
+    if constexpr (sizeof(T) == 2)
+      widen_halo_tile<K, S::ROWS, kThreads>(
+          sx, reinterpret_cast<const __nv_bfloat16*>(buf + ST::STAGE_OFF));
     if (use_tma && clamp &&
         (ty0 - G::R < 0 || ty0 + TH + G::R > H || tx0 - G::RP < 0 || tx0 + kTileW + G::RP > W))
-      clamp_fix<T, G::SP, kThreads>(sx, H, W, ty0, tx0, G::R, G::RP, S::ROWS);
+      clamp_fix<float, G::SP, kThreads>(sx, H, W, ty0, tx0, G::R, G::RP, S::ROWS);
     float acc[PY][4];
-    fwd_block<K, PY, T>(sx + warp * PY * G::SP + 4 * lane, sw, acc);
+    fwd_block<K, PY, float>(sx + warp * PY * G::SP + 4 * lane, sw, acc);
     store_block<T, PY>(y + plane * (int64_t)H * W, H, W, ty0 + warp * PY, tx0 + 4 * lane,
                        vec != 0, acc);
     cta_barrier();  // every warp is done with stage sb before it is refilled
   }
   cp_async_wait_group<0>();
   // after an abort: let a TMA load still in flight land (bounded) before exiting
-  if (*s_abort && use_tma && t + gridDim.x < num_tiles) mbar_wait(bars + (sb ^ 1), (phase >> (sb ^ 1)) & 1u);
+  if (*s_abort && use_tma && t + gridDim.x < num_tiles)
+    mbar_wait(bars + (sb ^ 1), (phase >> (sb ^ 1)) & 1u);
 }
 
 // -------------------------------------------------------------- backward
@@ -585,7 +657,7 @@ __global__ void __launch_bounds__(kThreads) dw_fwd_kernel(
 // cp.async with the border applied.
 template <int K, typename T>
 struct BwdShape {
-  using G = Geo<K, sizeof(T)>;
+  using G = Geo<K>;  // FP32 compute geometry
   static constexpr int NDX = 4;
   static constexpr int NDW = kWarps - NDX;
   static constexpr int GT = dw_groups<K>();
@@ -593,12 +665,13 @@ struct BwdShape {
   static constexpr int AT = (K + GT - 1) / GT;      // max filter rows per group
   static constexpr int DW_ROWS = kBwdTileH / WPG;   // tile rows per dw warp
   static constexpr int ROWS = kBwdTileH + 2 * G::R;  // x and dy tiles, both with the halo
-  static constexpr int TILE_BYTES = ROWS * G::SP * (int)sizeof(T);
-  // byte offsets: mbarrier and abort flag, staged tiles (TMA destinations
-  // 128-byte aligned), flipped filter and reduction in FP32
+  using ST = HaloTile<K, T, ROWS>;
+  // byte offsets: mbarrier and abort flag, the FP32 x and dy tiles (staged
+  // tiles at ST::STAGE_OFF inside them, 128-byte aligned for TMA), flipped
+  // filter and reduction
   static constexpr int SM_X = 128;
-  static constexpr int SM_DY = SM_X + round_up(TILE_BYTES, 128);
-  static constexpr int SM_W = SM_DY + round_up(TILE_BYTES, 16);
+  static constexpr int SM_DY = SM_X + ST::BYTES;
+  static constexpr int SM_W = SM_DY + ST::BYTES;
   static constexpr int SM_RED = SM_W + G::WPAD * 4;
   static constexpr int SM_BYTES = SM_RED + NDW * AT * K * 4;
   static_assert(NDW % GT == 0, "filter-row groups must divide the dw warps");
@@ -623,14 +696,18 @@ __global__ void __launch_bounds__(kThreads, bwd_min_ctas<T, K>())
                   float* __restrict__ partials, int C, int H, int W, int tiles_x,
                   int tiles_per_plane, int chunks_per_plane, int tpc, int clamp, int vec,
                   int use_tma, int* err) {
-  using G = Geo<K, sizeof(T)>;
+  using G = Geo<K>;
+  using GS = Geo<K, sizeof(T)>;
   using S = BwdShape<K, T>;
+  using ST = typename S::ST;
   extern __shared__ __align__(128) float smem[];
   char* sm = reinterpret_cast<char*>(smem);
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm);
   volatile int* s_abort = reinterpret_cast<volatile int*>(sm + 8);
-  T* sm_x = reinterpret_cast<T*>(sm + S::SM_X);
-  T* sm_dy = reinterpret_cast<T*>(sm + S::SM_DY);
+  float* sm_x = reinterpret_cast<float*>(sm + S::SM_X);
+  float* sm_dy = reinterpret_cast<float*>(sm + S::SM_DY);
+  T* st_x = reinterpret_cast<T*>(sm + S::SM_X + ST::STAGE_OFF);
+  T* st_dy = reinterpret_cast<T*>(sm + S::SM_DY + ST::STAGE_OFF);
   float* sm_w = reinterpret_cast<float*>(sm + S::SM_W);
   float* sm_red = reinterpret_cast<float*>(sm + S::SM_RED);
 
@@ -659,9 +736,9 @@ __global__ void __launch_bounds__(kThreads, bwd_min_ctas<T, K>())
       cp_async_commit();
       if (threadIdx.x == 0) {
         fence_proxy_async();
-        mbar_expect_tx(bar, (uint32_t)(2 * S::TILE_BYTES));
-        tma_load_3d(sm_x, &tmx, tx0 - G::RP, ty0 - G::R, (int)plane, bar);
-        tma_load_3d(sm_dy, &tmdy, tx0 - G::RP, ty0 - G::R, (int)plane, bar);
+        mbar_expect_tx(bar, (uint32_t)(2 * ST::STAGE_BYTES));
+        tma_load_3d(st_x, &tmx, tx0 - GS::RP, ty0 - G::R, (int)plane, bar);
+        tma_load_3d(st_dy, &tmdy, tx0 - GS::RP, ty0 - G::R, (int)plane, bar);
       }
       cp_async_wait_all();
       if (mbar_wait(bar, phase))
@@ -672,15 +749,21 @@ __global__ void __launch_bounds__(kThreads, bwd_min_ctas<T, K>())
       }
       cta_barrier();
       if (*s_abort) return false;
-      if (clamp && (ty0 - G::R < 0 || ty0 + kBwdTileH + G::R > H || tx0 - G::RP < 0 ||
-                    tx0 + kTileW + G::RP > W))
-        clamp_fix<T, G::SP, kThreads>(sm_x, H, W, ty0, tx0, G::R, G::RP, S::ROWS);
     } else {
-      stage_tile<T, G::R, G::RP, G::SP>(sm_x, xp, H, W, ty0, tx0, S::ROWS, clamp != 0,
-                                        vec != 0);
-      stage_tile<T, G::R, G::RP, G::SP>(sm_dy, dyp, H, W, ty0, tx0, S::ROWS, false, vec != 0);
+      stage_tile<T, G::R, GS::RP, GS::SP>(st_x, xp, H, W, ty0, tx0, S::ROWS, clamp != 0,
+                                          vec != 0);
+      stage_tile<T, G::R, GS::RP, GS::SP>(st_dy, dyp, H, W, ty0, tx0, S::ROWS, false,
+                                          vec != 0);
       stage_wait();
     }
+    if constexpr (sizeof(T) == 2) {
+      widen_halo_tile<K, S::ROWS, kThreads>(sm_x, reinterpret_cast<const __nv_bfloat16*>(st_x));
+      widen_halo_tile<K, S::ROWS, kThreads>(sm_dy, reinterpret_cast<const __nv_bfloat16*>(st_dy));
+    }
+    if (use_tma && clamp &&
+        (ty0 - G::R < 0 || ty0 + kBwdTileH + G::R > H || tx0 - G::RP < 0 ||
+         tx0 + kTileW + G::RP > W))
+      clamp_fix<float, G::SP, kThreads>(sm_x, H, W, ty0, tx0, G::R, G::RP, S::ROWS);
     return true;
   };
 
@@ -696,7 +779,7 @@ __global__ void __launch_bounds__(kThreads, bwd_min_ctas<T, K>())
       for (int pass = 0; pass < 16 / BR; ++pass) {
         const int r0 = warp * 16 + pass * BR;
         float acc[BR][4];
-        fwd_block<K, BR, T>(sm_dy + r0 * G::SP + 4 * lane, sm_w, acc);
+        fwd_block<K, BR, float>(sm_dy + r0 * G::SP + 4 * lane, sm_w, acc);
         store_block<T, BR>(dx + plane_off, H, W, ty0 + r0, tx0 + 4 * lane, vec != 0, acc);
       }
     }
@@ -719,7 +802,7 @@ __global__ void __launch_bounds__(kThreads, bwd_min_ctas<T, K>())
       if (!stage(ty0, tx0)) break;
       constexpr int BR = bwd_block_rows<K>();
       const int r0 = part * S::DW_ROWS;
-      dw_rows<K, S::AT, S::GT, G::SP, BR, T>(sm_dy + (r0 + G::R) * G::SP + G::RP + 4 * lane,
+      dw_rows<K, S::AT, S::GT, G::SP, BR, float>(sm_dy + (r0 + G::R) * G::SP + G::RP + 4 * lane,
                                              sm_x + (r0 + a_lo) * G::SP + 4 * lane,
                                              S::DW_ROWS / BR, nrows, acc);
     }
@@ -779,7 +862,7 @@ constexpr int filter_warps() {
 
 template <int K, typename T>
 struct FilterShape {
-  using G = Geo<K, sizeof(T)>;
+  using G = Geo<K, sizeof(T)>;  // tiles stay in the storage type (no widening pass)
   static constexpr int NW = filter_warps<K>();
   static constexpr int NT = NW * 32;
   static constexpr int GT = NW == 12 ? 3 : dw_groups<K>();
@@ -916,7 +999,7 @@ __global__ void __launch_bounds__(FilterShape<K, T>::NT, 1)
     const T* sdy = reinterpret_cast<const T*>(sm + sb * S::STAGE_BYTES + S::DY_OFF);
     if (use_tma && clamp && at_edge(cs))
       clamp_fix<T, G::SP, S::NT>(sx, H, W, (cs.t / tiles_x) * kFilterTileH,
-                                          (cs.t % tiles_x) * kTileW, G::R, G::RP, S::X_ROWS);
+                                 (cs.t % tiles_x) * kTileW, G::R, G::RP, S::X_ROWS);
     dw_rows<K, S::AT, S::GT, kTileW, S::DR, T>(sdy + part * S::ROWS * kTileW + 4 * lane,
                                                sx + (part * S::ROWS + a_lo) * G::SP + 4 * lane,
                                                S::ROWS / S::DR, nrows, acc);
