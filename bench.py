@@ -27,6 +27,13 @@ sys.path.insert(0, ROOT)
 
 N, C, H, W = 8, 3, 4096, 4096
 KS = (3, 7, 15)
+# DRAM bytes (read + written) per pixel of one launch, from the ncu capture of
+# one 1x3x4096x4096 launch of the kernel (dram__bytes_read.sum 201.38 MB +
+# dram__bytes_write.sum 157.27 MB); traffic grows with the pixel count, so a
+# launch over 8 such images moves 8x that.
+NCU_DRAM_BYTES_PER_PX = {
+    "dw_fwd_kernel<float,15,8>": (201383680 + 157269248) / (3 * 4096 * 4096),
+}
 METRIC = "Gpixel*tap/s fwd+bwd (depthwise KxK, K in {3,7,15})"
 UNIT = "Gpixel*tap/s"
 WORKLOAD = "plain_scale: 8x3x4096x4096 fp32, depthwise K in {3,7,15} normal(0,0.1), clamp border, fwd+bwd"
@@ -479,9 +486,16 @@ def run_giga(args):
     if cached:
         L.giga_autotune_set_mode(1)
         L.check(L.giga_autotune_load(args.tune_cache), "giga_autotune_load")
+    if args.pin_bwd is not None:
+        L.giga_autotune_set_mode(1)
     if not args.no_tune:
         for K in KS:
             d = descs[K]
+            if args.pin_bwd is not None:
+                L.check(L.giga_autotune_set_choice(d, L.GIGA_OP_BWD_INPUT | L.GIGA_OP_BWD_FILTER,
+                                                   args.pin_bwd), "giga_autotune_set_choice")
+                tuned[K] = {"fwd": L.giga_autotune_choice(d, L.GIGA_OP_FWD), "bwd": args.pin_bwd}
+                continue
             if cached:
                 tuned[K] = {"fwd": L.giga_autotune_choice(d, L.GIGA_OP_FWD),
                             "bwd": L.giga_autotune_choice(d, L.GIGA_OP_BWD_INPUT |
@@ -557,8 +571,11 @@ def run_giga(args):
         else:
             kernels.append((b["ms"] - f["ms"], f"dw_filter_kernel<float,{K}>", None))
     _, kname, dom = max((k for k in kernels if k[2] is not None), key=lambda k: k[0])
+    traffic = None
+    if kname in NCU_DRAM_BYTES_PER_PX and (H, W) == (4096, 4096):
+        traffic = NCU_DRAM_BYTES_PER_PX[kname] * px
     roofline = {"bound": dom["bound"], "achieved": dom["achieved"], "peak": dom["peak"],
-                "unit": dom["unit"], "frac": dom["frac"], "traffic": None,
+                "unit": dom["unit"], "frac": dom["frac"], "traffic": traffic,
                 "kernel": kname, "op": f"{dom['op']} K={dom['K']}",
                 "peak_source": (f"{pk['source']} HBM copy" if dom["bound"] == "hbm" else
                                 "FP32 FMA: 152 SMs x 128 lanes x 2 x max SM clock")}
@@ -710,6 +727,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="built-in default configurations")
+    ap.add_argument("--pin-bwd", type=int, default=None,
+                    help="backward configuration id for every K instead of tuning it "
+                         "(0-4: fused kernel, tiles per CTA auto/2/4/8/16; 5: two passes)")
     ap.add_argument("--tune-cache", default="",
                     help="autotune cache file: load it and skip tuning if it exists, "
                          "else tune and save the choices there")

@@ -200,6 +200,10 @@ giga_status_t giga_autotune_conv2d(const giga_conv2d_desc_t* desc, int32_t ops, 
 /* The configuration id the entry points will use for (desc, op): the cached
  * choice, else 0; -1 on error. */
 int32_t giga_autotune_choice(const giga_conv2d_desc_t* desc, int32_t op);
+/* Pin configuration `id` for (desc's problem class, op) in the cache, as if
+ * the tuner had chosen it; used in modes 1 and 2.  GIGA_ERR_INVALID_ARG for
+ * an unknown op or an id outside the op's candidates. */
+giga_status_t giga_autotune_set_choice(const giga_conv2d_desc_t* desc, int32_t op, int32_t id);
 giga_status_t giga_autotune_save(const char* path);
 giga_status_t giga_autotune_load(const char* path);
 void giga_autotune_clear(void);

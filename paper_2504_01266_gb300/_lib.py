@@ -41,7 +41,8 @@ EXPORTS = (
     "giga_batched_plan_workspace_size", "giga_batched_plan_upload", "giga_batched_plan_run",
     "giga_batched_plan_destroy", "giga_conv2d_batched", "giga_conv2d_batched_workspace_size",
     "giga_autotune_set_mode", "giga_autotune_get_mode", "giga_autotune_conv2d",
-    "giga_autotune_choice", "giga_autotune_save", "giga_autotune_load", "giga_autotune_clear",
+    "giga_autotune_choice", "giga_autotune_set_choice", "giga_autotune_save",
+    "giga_autotune_load", "giga_autotune_clear",
     "giga_status_string", "giga_check_device_error", "giga_selftest_bounded_wait",
     "giga_last_error_detail",
     "giga_launch_count",
@@ -98,6 +99,7 @@ _SIGS = {
     "giga_autotune_get_mode": (_I32, []),
     "giga_autotune_conv2d": (_ST, [_DESC, _I32, _P, _P, _P, _P, _P, _P, _P, _SZ, _P]),
     "giga_autotune_choice": (_I32, [_DESC, _I32]),
+    "giga_autotune_set_choice": (_ST, [_DESC, _I32, _I32]),
     "giga_autotune_save": (_ST, [ctypes.c_char_p]),
     "giga_autotune_load": (_ST, [ctypes.c_char_p]),
     "giga_autotune_clear": (None, []),
@@ -229,6 +231,10 @@ def giga_autotune_conv2d(d, ops, x, w, y, dy, dx, dw, ws, ws_bytes, stream) -> i
 
 def giga_autotune_choice(d, op) -> int:
     return int(load().giga_autotune_choice(ctypes.byref(d), op))
+
+
+def giga_autotune_set_choice(d, op, cand) -> int:
+    return load().giga_autotune_set_choice(ctypes.byref(d), op, cand)
 
 
 def giga_autotune_save(path: str) -> int:

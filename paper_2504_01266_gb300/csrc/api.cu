@@ -451,6 +451,19 @@ int32_t giga_autotune_choice(const giga_conv2d_desc_t* desc, int32_t op) {
   return id < 0 ? 0 : id;
 }
 
+giga_status_t giga_autotune_set_choice(const giga_conv2d_desc_t* desc, int32_t op, int32_t id) {
+  clear_error();
+  giga_status_t s = check_desc(desc);
+  if (s != GIGA_OK) return s;
+  if (!is_depthwise(desc)) return fail(GIGA_ERR_UNSUPPORTED, "only depthwise problems are tuned");
+  const int top = tune_op_of(op);
+  if (top < 0) return fail(GIGA_ERR_INVALID_ARG, "op must be 1, 2, 4 or 6");
+  if (id < 0 || id >= tune_candidates(top))
+    return fail(GIGA_ERR_INVALID_ARG, "configuration id " + std::to_string(id) + " out of range");
+  tune_store(top, make_args(desc), id);
+  return GIGA_OK;
+}
+
 const char* giga_status_string(giga_status_t status) {
   switch (status) {
     case GIGA_OK: return "success";

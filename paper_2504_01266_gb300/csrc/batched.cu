@@ -243,20 +243,10 @@ giga_status_t giga_batched_plan_run(giga_batched_plan_t plan, void* ws, size_t w
   p.n_chunks = (int)plan->chunks.size();
   p.ops = plan->ops;
   p.border = plan->border;
-  // the largest staged tile of the plan (every per-K shape grows with K)
-  size_t smem = 0;
-  switch (plan->max_k) {
-#define GIGA_RAG_SMEM(k)                                                                   \
-  case k:                                                                                  \
-    smem = plan->dtype == GIGA_F32 ? (size_t)RagShape<k, float>::SM_BYTES                 \
-                                   : (size_t)RagShape<k, __nv_bfloat16>::SM_BYTES;        \
-    break;
-    GIGA_RAG_SMEM(1) GIGA_RAG_SMEM(3) GIGA_RAG_SMEM(5) GIGA_RAG_SMEM(7) GIGA_RAG_SMEM(9)
-    GIGA_RAG_SMEM(11) GIGA_RAG_SMEM(13) GIGA_RAG_SMEM(15)
-#undef GIGA_RAG_SMEM
-    default:
-      return fail(GIGA_ERR_INVALID_ARG, "filter size above the batched limit");
-  }
+  if (plan->max_k > kRagMaxK) return fail(GIGA_ERR_INVALID_ARG, "filter size above the batched limit");
+  // one fixed layout, sized for the largest filter (two tile stages)
+  const size_t smem = plan->dtype == GIGA_F32 ? rag_max_smem<float>()
+                                               : rag_max_smem<__nv_bfloat16>();
   const int grid = (int)std::min<int64_t>((int64_t)sm_count(), (int64_t)plan->chunks.size());
   e = plan->dtype == GIGA_F32 ? rag_launch_f32(p, grid, smem, st)
                               : rag_launch_bf16(p, grid, smem, st);

@@ -34,14 +34,18 @@
 
 namespace giga {
 
+// Column halo of a K x K filter for elements of ES bytes: r rounded up to 16
+// bytes of elements (4 FP32, 8 BF16), so a staged row starts 16-byte aligned
+// in memory (TMA's rule for the x coordinate) and in shared memory.
+__host__ __device__ constexpr int geo_rp(int K, int ES) {
+  return ES == 2 ? ((K - 1) / 2 + 7) / 8 * 8 : ((K - 1) / 2 + 3) / 4 * 4;
+}
+
 // Tile geometry of a K x K filter for elements of ES bytes.
 template <int K, int ES = 4>
 struct Geo {
   static constexpr int R = (K - 1) / 2;
-  // column halo rounded up to 16 bytes of elements (4 FP32, 8 BF16), so a
-  // staged row starts 16-byte aligned in memory (TMA's rule for the x
-  // coordinate) and in shared memory
-  static constexpr int RP = ES == 2 ? (R + 7) / 8 * 8 : (R + 3) / 4 * 4;
+  static constexpr int RP = geo_rp(K, ES);
   static constexpr int SP = kTileW + 2 * RP;        // staged row pitch (elements)
   static constexpr int OFF = RP - R;                // first column a lane needs
   static constexpr int OFF4 = OFF / 4 * 4;          // whole 4-element chunks skipped
@@ -241,6 +245,73 @@ __device__ __forceinline__ void stage_tile(T* __restrict__ sm, const T* __restri
     }
   }
   if (COMMIT) cp_async_commit();
+}
+
+// stage_tile with the halo and pitch known only at run time (used where the
+// next tile's filter size is data-dependent); issues the copies, no commit.
+template <typename T, int NT>
+__device__ __forceinline__ void stage_tile_rt(T* __restrict__ sm, const T* __restrict__ plane,
+                                              int H, int W, int ty0, int tx0, int rows, int HR,
+                                              int HC, int pitch, bool clamp, bool vec) {
+  const int cpr = pitch / 4;
+  const int total = rows * cpr;
+  for (int k = threadIdx.x; k < total; k += NT) {
+    const int sr = k / cpr;
+    const int sc = (k - sr * cpr) * 4;
+    int gi = ty0 - HR + sr;
+    const int gj = tx0 - HC + sc;
+    T* dst = sm + sr * pitch + sc;
+    bool row_ok = gi >= 0 && gi < H;
+    if (!row_ok && clamp) {
+      gi = gi < 0 ? 0 : H - 1;
+      row_ok = true;
+    }
+    if constexpr (sizeof(T) == 4) {
+      if (!row_ok) {
+        cp_async16(reinterpret_cast<float*>(dst), plane, false);
+        continue;
+      }
+      const T* src = plane + (int64_t)gi * W;
+      if (vec && gj >= 0 && gj + 3 < W) {
+        cp_async16(reinterpret_cast<float*>(dst), src + gj, true);
+      } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          int j = gj + q;
+          bool ok = j >= 0 && j < W;
+          if (!ok && clamp) {
+            j = j < 0 ? 0 : W - 1;
+            ok = true;
+          }
+          cp_async4(reinterpret_cast<float*>(dst) + q, ok ? src + j : plane, ok);
+        }
+      }
+    } else {
+      if (!row_ok) {
+        cp_async8(dst, plane, false);
+        continue;
+      }
+      const T* src = plane + (int64_t)gi * W;
+      if (vec && gj >= 0 && gj + 3 < W) {
+        cp_async8(dst, src + gj, true);
+      } else {
+        Tile<T>::store4(dst, load_chunk<T>(plane, H, W, gi, gj, clamp, vec));
+      }
+    }
+  }
+}
+
+// A K x K filter (K known at run time) with rows padded to a multiple of 4
+// (zeros), optionally rotated by 180 degrees; cp.async, no commit.
+template <int NT>
+__device__ __forceinline__ void stage_filter_rt(float* __restrict__ sm,
+                                                const float* __restrict__ w, int K, bool flip) {
+  const int kp = (K + 3) / 4 * 4;
+  for (int k = threadIdx.x; k < K * kp; k += NT) {
+    const int a = k / kp, b = k - (k / kp) * kp;
+    const bool ok = b < K;
+    cp_async4(sm + k, ok ? w + (flip ? (K - 1 - a) * K + (K - 1 - b) : a * K + b) : w, ok);
+  }
 }
 
 // Staged-tile layout of storage type T in a buffer sized for the FP32 tile of

@@ -61,109 +61,142 @@ struct RagShape {
   static constexpr int AT = (K + GT - 1) / GT;
   static constexpr int DW_ROWS = kBwdTileH / WPG;
   static constexpr int ROWS = kBwdTileH + 2 * G::R;
-  // byte offsets: staged tiles in the storage type, filters and reduction FP32
-  static constexpr int SM_X = 0;
-  static constexpr int SM_DY = ROWS * G::SP * (int)sizeof(T);
-  static constexpr int SM_W = 2 * ROWS * G::SP * (int)sizeof(T);
-  static constexpr int SM_WF = SM_W + G::WPAD * 4;
-  static constexpr int SM_RED = SM_WF + G::WPAD * 4;
-  static constexpr int SM_BYTES = SM_RED + 4 * AT * K * 4;
+};
+
+// Shared memory, sized for the largest filter: two tile stages (x and dy
+// tiles), two filter buffers (a chunk's filter and its rotation; indexed by
+// chunk parity so the next chunk's filter can be staged while the current one
+// is in use), the filter-gradient reduction rows and two ints.
+template <typename T>
+struct RagLayout {
+  using G = Geo<kRagMaxK, sizeof(T)>;
+  static constexpr int TILE = round_up((kBwdTileH + 2 * G::R) * G::SP * (int)sizeof(T), 128);
+  static constexpr int STAGE = 2 * TILE;          // x, then dy
+  static constexpr int WB = G::WPAD * 4;          // one filter
+  static constexpr int FILT = 2 * STAGE;          // [2][w, wf]
+  static constexpr int RED = FILT + 4 * WB;       // 4 dw warps x max(AT * K) floats
+  static constexpr int RED_FLOATS = 66;           // K = 11: 6 rows x 11 taps
+  static constexpr int INTS = RED + 4 * RED_FLOATS * 4;
+  static constexpr int SM_BYTES = INTS + 16;
+  static_assert(RagShape<11, T>::AT * 11 <= RED_FLOATS && RagShape<15, T>::AT * 15 <= RED_FLOATS,
+                "reduction rows");
+  static_assert(SM_BYTES <= 227 * 1024, "shared memory");
 };
 
 template <typename T>
 constexpr size_t rag_max_smem() {
-  return (size_t)RagShape<15, T>::SM_BYTES;
+  return (size_t)RagLayout<T>::SM_BYTES;
 }
 
+// Issue the copies of tile t of chunk ch (image im) into stage sb and, for the
+// first tile of a chunk, its filters into filter buffer fb (no commit).
+template <typename T>
+__device__ __forceinline__ void rag_stage(const RagParams& p, const RagChunk& ch,
+                                          const RagImage& im, int t, char* sm, int sb, int fb,
+                                          bool filters) {
+  using L = RagLayout<T>;
+  const int K = im.K, R = (K - 1) / 2, RP = geo_rp(K, sizeof(T)), SP = kTileW + 2 * RP;
+  const int H = im.H, W = im.W;
+  const int tiles_x = (W + kTileW - 1) / kTileW;
+  const int ty0 = (t / tiles_x) * kBwdTileH, tx0 = (t % tiles_x) * kTileW;
+  const int64_t off = (int64_t)ch.channel * H * W;
+  const bool do_fwd = p.ops & 1, do_dx = p.ops & 2, do_dw = p.ops & 4;
+  const bool clamp = p.border == 1, vec = im.vec != 0;
+  T* sx = reinterpret_cast<T*>(sm + sb * L::STAGE);
+  T* sdy = reinterpret_cast<T*>(sm + sb * L::STAGE + L::TILE);
+  if (do_fwd || do_dw)
+    stage_tile_rt<T, kRagThreads>(sx, static_cast<const T*>(im.x) + off, H, W, ty0, tx0,
+                                  kBwdTileH + 2 * R, R, RP, SP, clamp, vec);
+  if (do_dx || do_dw)
+    stage_tile_rt<T, kRagThreads>(sdy, static_cast<const T*>(im.dy) + off, H, W, ty0, tx0,
+                                  kBwdTileH + 2 * R, R, RP, SP, false, vec);
+  // w may be NULL when neither the forward nor the input gradient is requested
+  if (filters && (do_fwd || do_dx)) {
+    const float* wc = im.w + (int64_t)ch.channel * K * K;
+    float* f = reinterpret_cast<float*>(sm + L::FILT + fb * 2 * L::WB);
+    stage_filter_rt<kRagThreads>(f, wc, K, false);
+    stage_filter_rt<kRagThreads>(f + L::WB / 4, wc, K, true);
+  }
+}
+
+// One chunk: its first tile is already in stage sb (copies in flight), its
+// filters in filter buffer fb.  While tile t is computed, the copies of the
+// next tile -- the next of this chunk, or the first of chunk `cn` -- go to
+// the other stage.  Returns the stage holding the next chunk's first tile.
 template <typename T, int K>
-__device__ __forceinline__ void rag_chunk(const RagParams& p, const RagChunk& ch,
-                                          const RagImage& im, float* smem, int* s_flag) {
+__device__ __forceinline__ int rag_chunk(const RagParams& p, const RagChunk& ch,
+                                         const RagImage& im, int cn, char* sm, int sb, int fb,
+                                         int* s_flag) {
   using G = Geo<K, sizeof(T)>;
   using S = RagShape<K, T>;
+  using L = RagLayout<T>;
   constexpr int KK = K * K;
-  char* sm = reinterpret_cast<char*>(smem);
-  T* sm_x = reinterpret_cast<T*>(sm + S::SM_X);
-  T* sm_dy = reinterpret_cast<T*>(sm + S::SM_DY);
-  float* sm_w = reinterpret_cast<float*>(sm + S::SM_W);
-  float* sm_wf = reinterpret_cast<float*>(sm + S::SM_WF);
-  float* sm_red = reinterpret_cast<float*>(sm + S::SM_RED);
+  float* sm_red = reinterpret_cast<float*>(sm + L::RED);
+  const float* sm_w = reinterpret_cast<const float*>(sm + L::FILT + fb * 2 * L::WB);
+  const float* sm_wf = sm_w + L::WB / 4;
 
   const int H = im.H, W = im.W;
   const int tiles_x = (W + kTileW - 1) / kTileW;
   const int64_t off = (int64_t)ch.channel * H * W;
   const bool do_fwd = p.ops & 1, do_dx = p.ops & 2, do_dw = p.ops & 4;
-  const bool need_x = do_fwd || do_dw, need_dy = do_dx || do_dw;
   const bool clamp = p.border == 1, vec = im.vec != 0;
-  const T* xp = need_x ? static_cast<const T*>(im.x) + off : nullptr;
-  const T* dyp = need_dy ? static_cast<const T*>(im.dy) + off : nullptr;
   T* yp = do_fwd ? static_cast<T*>(im.y) + off : nullptr;
   T* dxp = do_dx ? static_cast<T*>(im.dx) + off : nullptr;
-  // w may be NULL when neither the forward nor the input gradient is requested
   const float* wc = (do_fwd || do_dx) ? im.w + (int64_t)ch.channel * KK : nullptr;
-  if (wc) {
-    stage_filter<K>(sm_w, wc, false, kRagThreads);
-    stage_filter<K>(sm_wf, wc, true, kRagThreads);
-  }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int role = warp >> 2, wl = warp & 3;
+  const int g = wl % S::GT;
+  const int part = wl / S::GT;
+  const int a_lo = group_lo(g, K, S::GT);
+  const int nrows = group_lo(g + 1, K, S::GT) - a_lo;
+  float acc[S::AT][K];
+#pragma unroll
+  for (int s = 0; s < S::AT; ++s)
+#pragma unroll
+    for (int b = 0; b < K; ++b) acc[s][b] = 0.f;
 
-  if (role < 2) {
-    const bool active = role == 0 ? do_fwd : do_dx;
-    const T* src = role == 0 ? sm_x : sm_dy;
-    const float* f = role == 0 ? sm_w : sm_wf;
-    T* dst = role == 0 ? yp : dxp;
-    for (int t = ch.tile_begin; t < ch.tile_end; ++t) {
-      const int ty0 = (t / tiles_x) * kBwdTileH, tx0 = (t % tiles_x) * kTileW;
-      cta_barrier();
-      if (need_x)
-        stage_tile<T, G::R, G::RP, G::SP, kRagThreads>(sm_x, xp, H, W, ty0, tx0, S::ROWS, clamp,
-                                                       vec);
-      if (need_dy)
-        stage_tile<T, G::R, G::RP, G::SP, kRagThreads>(sm_dy, dyp, H, W, ty0, tx0, S::ROWS,
-                                                       false, vec);
-      stage_wait();
-      if (active) {
+  for (int t = ch.tile_begin; t < ch.tile_end; ++t) {
+    if (t + 1 < ch.tile_end) {
+      rag_stage<T>(p, ch, im, t + 1, sm, sb ^ 1, fb, false);
+    } else if (cn < p.n_chunks) {
+      const RagChunk chn = p.chunks[cn];
+      const RagImage imn = p.images[chn.image];
+      rag_stage<T>(p, chn, imn, chn.tile_begin, sm, sb ^ 1, fb ^ 1, true);
+    }
+    cp_async_commit();
+    cp_async_wait_group<1>();  // this tile's copies (committed one tile earlier) have landed
+    cta_barrier();
+    const T* sx = reinterpret_cast<const T*>(sm + sb * L::STAGE);
+    const T* sdy = reinterpret_cast<const T*>(sm + sb * L::STAGE + L::TILE);
+    const int ty0 = (t / tiles_x) * kBwdTileH, tx0 = (t % tiles_x) * kTileW;
+    if (role < 2) {
+      if (role == 0 ? do_fwd : do_dx) {
+        const T* src = role == 0 ? sx : sdy;
+        const float* f = role == 0 ? sm_w : sm_wf;
+        T* dst = role == 0 ? yp : dxp;
         constexpr int BR = bwd_block_rows<K>();
 #pragma unroll 1
         for (int pass = 0; pass < 16 / BR; ++pass) {
           const int r0 = wl * 16 + pass * BR;
-          float acc[BR][4];
-          fwd_block<K, BR, T>(src + r0 * G::SP + 4 * lane, f, acc);
-          store_block<T, BR>(dst, H, W, ty0 + r0, tx0 + 4 * lane, vec, acc);
+          float o[BR][4];
+          fwd_block<K, BR, T>(src + r0 * G::SP + 4 * lane, f, o);
+          store_block<T, BR>(dst, H, W, ty0 + r0, tx0 + 4 * lane, vec, o);
         }
       }
+    } else if (do_dw) {
+      constexpr int BR = bwd_block_rows<K>();
+      const int r0 = part * S::DW_ROWS;
+      dw_rows<K, S::AT, S::GT, G::SP, BR, T>(sdy + (r0 + G::R) * G::SP + G::RP + 4 * lane,
+                                             sx + (r0 + a_lo) * G::SP + 4 * lane,
+                                             S::DW_ROWS / BR, nrows, acc);
     }
-    cta_barrier();
-    cta_barrier();
-  } else {
-    const int g = wl % S::GT;
-    const int part = wl / S::GT;
-    const int a_lo = group_lo(g, K, S::GT);
-    const int nrows = group_lo(g + 1, K, S::GT) - a_lo;
-    float acc[S::AT][K];
-#pragma unroll
-    for (int s = 0; s < S::AT; ++s)
-#pragma unroll
-      for (int b = 0; b < K; ++b) acc[s][b] = 0.f;
-    for (int t = ch.tile_begin; t < ch.tile_end; ++t) {
-      const int ty0 = (t / tiles_x) * kBwdTileH, tx0 = (t % tiles_x) * kTileW;
-      cta_barrier();
-      if (need_x)
-        stage_tile<T, G::R, G::RP, G::SP, kRagThreads>(sm_x, xp, H, W, ty0, tx0, S::ROWS, clamp,
-                                                       vec);
-      if (need_dy)
-        stage_tile<T, G::R, G::RP, G::SP, kRagThreads>(sm_dy, dyp, H, W, ty0, tx0, S::ROWS,
-                                                       false, vec);
-      stage_wait();
-      if (do_dw) {
-        constexpr int BR = bwd_block_rows<K>();
-        const int r0 = part * S::DW_ROWS;
-        dw_rows<K, S::AT, S::GT, G::SP, BR, T>(sm_dy + (r0 + G::R) * G::SP + G::RP + 4 * lane,
-                                               sm_x + (r0 + a_lo) * G::SP + 4 * lane,
-                                               S::DW_ROWS / BR, nrows, acc);
-      }
-    }
-    cta_barrier();
+    cta_barrier();  // stage sb is free for the copies two tiles ahead
+    sb ^= 1;
+  }
+
+  // filter-gradient partial of this chunk: warp butterflies, then a fixed-order
+  // sum over the group's warps
+  if (role == 2 && do_dw) {
 #pragma unroll
     for (int s = 0; s < S::AT; ++s)
 #pragma unroll
@@ -171,22 +204,21 @@ __device__ __forceinline__ void rag_chunk(const RagParams& p, const RagChunk& ch
         float v = acc[s][b];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) sm_red[(wl * S::AT + s) * K + b] = v;
+        if (lane == 0) sm_red[wl * L::RED_FLOATS + s * K + b] = v;
       }
-    cta_barrier();
   }
-
+  cta_barrier();
   const int ic = im.ic_base + ch.channel;
   float* part_c = p.partials + im.partial_base + (int64_t)ch.channel * im.nch * KK;
   if (do_dw) {
     const int j = ch.tile_begin / kRagTilesPerChunk;
     for (int k = threadIdx.x; k < KK; k += kRagThreads) {
       const int a = k / K, b = k - (k / K) * K;
-      int g = 0;
-      while (g + 1 < S::GT && group_lo(g + 1, K, S::GT) <= a) ++g;
-      const int s = a - group_lo(g, K, S::GT);
+      int gg = 0;
+      while (gg + 1 < S::GT && group_lo(gg + 1, K, S::GT) <= a) ++gg;
+      const int s = a - group_lo(gg, K, S::GT);
       float sum = 0.f;
-      for (int q = 0; q < S::WPG; ++q) sum += sm_red[((q * S::GT + g) * S::AT + s) * K + b];
+      for (int q = 0; q < S::WPG; ++q) sum += sm_red[(q * S::GT + gg) * L::RED_FLOATS + s * K + b];
       part_c[(int64_t)j * KK + k] = sum;
     }
   }
@@ -206,37 +238,56 @@ __device__ __forceinline__ void rag_chunk(const RagParams& p, const RagChunk& ch
       }
       if (do_dx && clamp) {
         const int64_t edges = edge_pixels(H, W);
-        const T* g = static_cast<const T*>(im.dy) + off;
+        const T* gsrc = static_cast<const T*>(im.dy) + off;
         for (int64_t e = threadIdx.x; e < edges; e += kRagThreads)
-          fold_edge_pixel<T>(g, wc, dxp, H, W, K, e);
+          fold_edge_pixel<T>(gsrc, wc, dxp, H, W, K, e);
       }
     }
   }
+  cta_barrier();  // sm_red and s_flag are reused by the next chunk
+  return sb;
 }
 
 template <typename T>
 __global__ void __launch_bounds__(kRagThreads, 1) rag_kernel(RagParams p) {
-  extern __shared__ __align__(16) float smem[];
-  __shared__ int s_idx, s_flag;
+  extern __shared__ __align__(128) float smem[];
+  using L = RagLayout<T>;
+  char* sm = reinterpret_cast<char*>(smem);
+  volatile int* s_next = reinterpret_cast<volatile int*>(sm + L::INTS);
+  int* s_flag = reinterpret_cast<int*>(sm + L::INTS + 4);
+  if (threadIdx.x == 0) *s_next = atomicAdd(p.counters, 1);
+  cta_barrier();
+  int c = *s_next;
+  if (c >= p.n_chunks) return;
+  int sb = 0, fb = 0;
+  {
+    const RagChunk ch = p.chunks[c];
+    const RagImage im = p.images[ch.image];
+    rag_stage<T>(p, ch, im, ch.tile_begin, sm, sb, fb, true);
+    cp_async_commit();
+  }
   for (;;) {
-    if (threadIdx.x == 0) s_idx = atomicAdd(p.counters, 1);
+    cta_barrier();  // every thread has read the previous *s_next
+    if (threadIdx.x == 0) *s_next = atomicAdd(p.counters, 1);  // one chunk ahead
     cta_barrier();
-    const int idx = s_idx;
-    if (idx >= p.n_chunks) break;
-    const RagChunk ch = p.chunks[idx];
+    const int cn = *s_next;
+    const RagChunk ch = p.chunks[c];
     const RagImage im = p.images[ch.image];
     switch (im.K) {
-      case 1: rag_chunk<T, 1>(p, ch, im, smem, &s_flag); break;
-      case 3: rag_chunk<T, 3>(p, ch, im, smem, &s_flag); break;
-      case 5: rag_chunk<T, 5>(p, ch, im, smem, &s_flag); break;
-      case 7: rag_chunk<T, 7>(p, ch, im, smem, &s_flag); break;
-      case 9: rag_chunk<T, 9>(p, ch, im, smem, &s_flag); break;
-      case 11: rag_chunk<T, 11>(p, ch, im, smem, &s_flag); break;
-      case 13: rag_chunk<T, 13>(p, ch, im, smem, &s_flag); break;
-      default: rag_chunk<T, 15>(p, ch, im, smem, &s_flag); break;
+      case 1: sb = rag_chunk<T, 1>(p, ch, im, cn, sm, sb, fb, s_flag); break;
+      case 3: sb = rag_chunk<T, 3>(p, ch, im, cn, sm, sb, fb, s_flag); break;
+      case 5: sb = rag_chunk<T, 5>(p, ch, im, cn, sm, sb, fb, s_flag); break;
+      case 7: sb = rag_chunk<T, 7>(p, ch, im, cn, sm, sb, fb, s_flag); break;
+      case 9: sb = rag_chunk<T, 9>(p, ch, im, cn, sm, sb, fb, s_flag); break;
+      case 11: sb = rag_chunk<T, 11>(p, ch, im, cn, sm, sb, fb, s_flag); break;
+      case 13: sb = rag_chunk<T, 13>(p, ch, im, cn, sm, sb, fb, s_flag); break;
+      default: sb = rag_chunk<T, 15>(p, ch, im, cn, sm, sb, fb, s_flag); break;
     }
-    cta_barrier();
+    if (cn >= p.n_chunks) break;
+    c = cn;
+    fb ^= 1;
   }
+  cp_async_wait_group<0>();
 }
 
 cudaError_t rag_launch_f32(const RagParams& p, int grid, size_t smem, cudaStream_t st);

@@ -125,6 +125,26 @@ def test_autotune_cache_roundtrip_and_corruption(lib, tmp_path):
         _lib.giga_autotune_set_mode(7)
 
 
+def test_autotune_set_choice(lib):
+    _lib.giga_autotune_clear()
+    mode = _lib.giga_autotune_get_mode()
+    _lib.giga_autotune_set_mode(1)
+    try:
+        d = dw(N=2, C=3, H=256, W=512, K=15)
+        fused = _lib.GIGA_OP_BWD_INPUT | _lib.GIGA_OP_BWD_FILTER
+        assert _lib.giga_autotune_set_choice(d, fused, 5) == _lib.GIGA_OK
+        assert _lib.giga_autotune_choice(d, fused) == 5
+        assert _lib.giga_autotune_choice(d, _lib.GIGA_OP_FWD) == 0  # other ops untouched
+        assert _lib.giga_autotune_set_choice(d, _lib.GIGA_OP_FWD, 4) == _lib.GIGA_ERR_INVALID_ARG
+        assert _lib.giga_autotune_set_choice(d, _lib.GIGA_OP_BWD_FILTER, 5) == \
+            _lib.GIGA_ERR_INVALID_ARG
+        assert _lib.giga_autotune_set_choice(d, 3, 0) == _lib.GIGA_ERR_INVALID_ARG
+        assert _lib.giga_autotune_set_choice(d, _lib.GIGA_OP_FWD, -1) == _lib.GIGA_ERR_INVALID_ARG
+    finally:
+        _lib.giga_autotune_clear()
+        _lib.giga_autotune_set_mode(mode)
+
+
 def test_empty_problem_launches_nothing(lib):
     d = dw(N=0)
     _lib.giga_launch_count_reset()
