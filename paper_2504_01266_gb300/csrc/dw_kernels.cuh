@@ -924,11 +924,16 @@ constexpr int kFilterTileH = 64;
 static_assert(kFilterTileH == kBwdTileH, "both filter-gradient kernels share the chunk layout");
 
 // Warps and tap-row groups: K = 9 and 15 split into 3 equal groups (12 warps,
-// up to 170 registers for the larger accumulator set); the rest use 16 warps
-// and dw_groups<K>().
+// up to 170 registers for the larger accumulator set: measured faster than 5
+// groups of 3 rows on 20 warps at 96 registers); the rest use 16 warps and
+// dw_groups<K>().
 template <int K>
 constexpr int filter_warps() {
   return (K == 9 || K == 15) ? 12 : 16;
+}
+template <int K>
+constexpr int filter_groups() {
+  return (K == 9 || K == 15) ? 3 : dw_groups<K>();
 }
 
 template <int K, typename T>
@@ -936,7 +941,7 @@ struct FilterShape {
   using G = Geo<K, sizeof(T)>;  // tiles stay in the storage type (no widening pass)
   static constexpr int NW = filter_warps<K>();
   static constexpr int NT = NW * 32;
-  static constexpr int GT = NW == 12 ? 3 : dw_groups<K>();
+  static constexpr int GT = filter_groups<K>();
   static constexpr int WPG = NW / GT;
   static constexpr int AT = (K + GT - 1) / GT;
   static constexpr int ROWS = kFilterTileH / WPG;  // tile rows per warp
