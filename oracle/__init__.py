@@ -80,6 +80,8 @@ def _load():
             "oracle_dense_bwd_input_points": [_D, _D] + dense + [_I64P, _I64, _D],
             "oracle_dense_bwd_filter": [_D, _D, _D] + dense,
             "oracle_dense_bwd_filter_taps": [_D, _D] + dense + [_I64P, _I64, _D],
+            "oracle_upsample_nearest": [_D, _D, _I64, _I64, _I64, _I64],
+            "oracle_upsample_dw_fwd_points": [_D, _D] + six + [_I64, _I64P, _I64, _D],
         }
         for name, args in sigs.items():
             fn = getattr(lib, name)
@@ -291,6 +293,7 @@ class use_library:
                      "oracle_dw_bwd_filter_taps", "oracle_dense_fwd", "oracle_dense_fwd_points",
                      "oracle_dense_bwd_input", "oracle_dense_bwd_input_points",
                      "oracle_dense_bwd_filter", "oracle_dense_bwd_filter_taps",
+                     "oracle_upsample_nearest", "oracle_upsample_dw_fwd_points",
                      "oracle_num_threads"):
             src, dst = getattr(self.saved, name), getattr(lib, name)
             dst.argtypes, dst.restype = src.argtypes, src.restype
@@ -303,3 +306,33 @@ class use_library:
         with _lock:
             _lib = self.saved
         return False
+
+
+# ----------------------------------------------------------------- upsampling
+
+def upsample_nearest(x, s: int) -> np.ndarray:
+    """Nearest-neighbour upsampling by the integer factor s over the last two
+    axes (Section 4.2.3): out[..., p, q] = x[..., p // s, q // s]."""
+    x = _f64(x)
+    *lead, H, W = x.shape
+    planes = int(np.prod(lead)) if lead else 1
+    y = np.empty((*lead, H * s, W * s), dtype=np.float64)
+    _check(_load().oracle_upsample_nearest(_p(x), _p(y), planes, H, W, s), "upsample_nearest")
+    return y
+
+
+def upsample_dw_fwd(x, w, border: int, s: int) -> np.ndarray:
+    """The sharpening benchmark (Section 6.6): upsample, then filter."""
+    return dw_fwd(upsample_nearest(x, s), w, border)
+
+
+def upsample_dw_fwd_points(x, w, border: int, s: int, idx) -> np.ndarray:
+    """``upsample_dw_fwd`` at flat NCHW indices of the (N, C, H*s, W*s) result."""
+    x, w, idx = _f64(x), _f64(w), _i64(idx)
+    K = _filter_size(w)
+    N, C, H, W = _dw_shape(x, w, K)
+    out = np.empty(idx.size, dtype=np.float64)
+    _check(_load().oracle_upsample_dw_fwd_points(_p(x), _p(w), N, C, H, W, K, border, s,
+                                                 _pi(idx), idx.size, _p(out)),
+           "upsample_dw_fwd_points")
+    return out

@@ -20,7 +20,10 @@
  *     input (the transpose of the forward operator) and the gradient with
  *     respect to the filter;
  *   - the dense multi-channel case (every output channel sums over every input
- *     channel), which is the same neighbourhood sum with one more index.
+ *     channel), which is the same neighbourhood sum with one more index;
+ *   - nearest-neighbour upsampling by an integer factor (Section 4.2.3), and
+ *     the paper's sharpening benchmark (Section 6.6): the filter applied to
+ *     the upsampled image.
  *
  * Conventions (plain definitions, no blocking or reordering):
  *   r = (K - 1) / 2, tap (a, b) with a, b in [0, K) reads the neighbour at
@@ -382,6 +385,56 @@ int oracle_dense_bwd_input_points(const double* dy, const double* w, int64_t N, 
             }
         }
         out[t] = sum;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------- upsampling */
+
+/* Nearest-neighbour upsampling by an integer factor s >= 1 (Section 4.2.3):
+ * every pixel of the (H*s) x (W*s) output copies the input pixel found by
+ * dividing its coordinates by s (integer division), plane by plane. */
+int oracle_upsample_nearest(const double* x, double* y, int64_t planes, int64_t H, int64_t W,
+                            int64_t s) {
+    if (planes < 0 || H < 0 || W < 0 || s < 1) return 1;
+    const int64_t Ho = H * s, Wo = W * s;
+#pragma omp parallel for schedule(static)
+    for (int64_t pl = 0; pl < planes; ++pl)
+        for (int64_t p = 0; p < Ho; ++p)
+            for (int64_t q = 0; q < Wo; ++q)
+                y[(pl * Ho + p) * Wo + q] = x[(pl * H + p / s) * W + q / s];
+    return 0;
+}
+
+/* The sharpening benchmark's output at selected flat NCHW indices of the
+ * (N, C, H*s, W*s) result: the depthwise filter applied to the upsampled
+ * image, with the border rule on the upsampled image.  The upsampled pixel
+ * (u, v) is read as x[u / s][v / s], so the upsampled image is never built. */
+int oracle_upsample_dw_fwd_points(const double* x, const double* w, int64_t N, int64_t C,
+                                  int64_t H, int64_t W, int K, int border, int64_t s,
+                                  const int64_t* idx, int64_t count, double* out) {
+    if (check_args(N, C, H, W, K, border) || s < 1) return 1;
+    const int64_t Ho = H * s, Wo = W * s;
+    const int r = (K - 1) / 2;
+#pragma omp parallel for schedule(static)
+    for (int64_t k = 0; k < count; ++k) {
+        int64_t t = idx[k];
+        const int64_t j = t % Wo; t /= Wo;
+        const int64_t i = t % Ho; t /= Ho;
+        const int64_t c = t % C, n = t / C;
+        const double* plane = x + (n * C + c) * H * W;
+        const double* f = w + c * (int64_t)K * K;
+        double sum = 0.0;
+        for (int a = 0; a < K; ++a) {
+            int64_t su;
+            if (!border_source(i + a - r, Ho, border, &su)) continue;
+            for (int b = 0; b < K; ++b) {
+                int64_t sv;
+                if (!border_source(j + b - r, Wo, border, &sv)) continue;
+                sum += f[a * K + b] * plane[(su / s) * W + sv / s];
+            }
+        }
+        out[k] = sum;
     }
     return 0;
 }

@@ -1,9 +1,11 @@
 """Pins for the FP64 oracle, checked against facts the oracle does not compute
 itself: hand-derived fixtures (tests/golden), closed forms, identities of the
-mathematics, an independent library routine (torch's FP64 CPU convolution)
-and brute force on tiny inputs.  The operation is the neighbourhood sum of the
-GigaAPI paper, Section 4.2.4 ("Sharpening"), widened to K x K depthwise and
-dense filters, zero/clamp borders and the two gradients.
+mathematics, independent library routines (torch's FP64 CPU convolution and
+nearest interpolation, numpy's repeat) and brute force on tiny inputs.  The
+operation is the neighbourhood sum of the GigaAPI paper, Section 4.2.4
+("Sharpening"), widened to K x K depthwise and dense filters, zero/clamp
+borders and the two gradients, plus the nearest-neighbour upsampling of
+Section 4.2.3 and the upsample-then-sharpen benchmark of Section 6.6.
 
 Each ``pin_*`` function raises AssertionError when the oracle is wrong; the
 pytest tests call them, and the mutation test at the bottom plants typical
@@ -317,10 +319,56 @@ def pin_dense():
                                               border)[:, 0]) < 1e-14
 
 
+def pin_upsample_nearest():
+    """Nearest-neighbour upsampling (Section 4.2.3) against numpy's repeat and
+    torch's FP64 nearest interpolation (both library routines), the identity at
+    scale 1, and the structure of the result: constant s x s blocks whose
+    stride-s subsampling gives back the input."""
+    g = rng(21)
+    for shape in [(1, 2, 5, 7), (2, 1, 3, 4), (1, 3, 1, 1)]:
+        x = g.standard_normal(shape)
+        assert np.array_equal(oracle.upsample_nearest(x, 1), x)
+        for s in (2, 3, 5):
+            up = oracle.upsample_nearest(x, s)
+            assert up.shape == shape[:2] + (shape[2] * s, shape[3] * s)
+            assert np.array_equal(up, np.repeat(np.repeat(x, s, axis=-2), s, axis=-1)), (shape, s)
+            t = F.interpolate(torch.from_numpy(x), scale_factor=s, mode="nearest").numpy()
+            assert np.array_equal(up, t), (shape, s)
+            assert np.array_equal(up[..., ::s, ::s], x)
+            for a in range(s):
+                for b in range(s):
+                    assert np.array_equal(up[..., a::s, b::s], x)
+
+
+def pin_upsample_sharpen():
+    """The sharpening benchmark (Section 6.6) = upsample, then filter: against
+    torch's FP64 nearest interpolation followed by its FP64 depthwise
+    convolution, and the point evaluations against the full arrays; the paper's
+    Laplacian on an upsampled constant image is 0 wherever its 3 x 3 window
+    stays inside the image."""
+    g = rng(22)
+    for K in (1, 3, 5):
+        for s in (1, 2, 3):
+            x = g.standard_normal((1, 2, 4, 6))
+            w = g.standard_normal((2, K, K))
+            xt = F.interpolate(torch.from_numpy(x), scale_factor=s, mode="nearest").numpy()
+            for border in (ZERO, CLAMP):
+                full = oracle.upsample_dw_fwd(x, w, border, s)
+                assert rel(full, torch_dw(xt, w, border)) < 1e-13, (K, s, border)
+                idx = np.arange(full.size)[::7]
+                pts = oracle.upsample_dw_fwd_points(x, w, border, s, idx)
+                assert np.array_equal(pts, full.reshape(-1)[idx]), (K, s, border)
+    lap = np.array([[[-1.0, -1, -1], [-1, 8, -1], [-1, -1, -1]]])
+    const = np.full((1, 1, 3, 5), 2.5)
+    y = oracle.upsample_dw_fwd(const, lap, ZERO, 4)
+    assert np.all(y[..., 1:-1, 1:-1] == 0.0)
+    assert np.all(oracle.upsample_dw_fwd(const, lap, CLAMP, 4) == 0.0)
+
+
 PINS = [pin_golden, pin_delta, pin_shift, pin_box_constant, pin_torch_crosscheck,
         pin_separable_gaussian, pin_linearity, pin_translation, pin_operator_bruteforce,
         pin_adjoint, pin_filter_bilinear, pin_finite_differences, pin_points_match_full,
-        pin_dense]
+        pin_dense, pin_upsample_nearest, pin_upsample_sharpen]
 
 
 @pytest.mark.parametrize("pin", PINS, ids=[p.__name__ for p in PINS])
@@ -366,6 +414,15 @@ MUTATIONS = {
     "dense_taps_transposed": (
         "const double* f = w + ((o * K + a) * (int64_t)K + b) * Ci;\n            for (int64_t c = 0; c < Ci; ++c) sum",
         "const double* f = w + ((o * K + b) * (int64_t)K + a) * Ci;\n            for (int64_t c = 0; c < Ci; ++c) sum"),
+    "upsample_coordinates_swapped": (
+        "y[(pl * Ho + p) * Wo + q] = x[(pl * H + p / s) * W + q / s];",
+        "y[(pl * Ho + p) * Wo + q] = x[(pl * H + q / s % H) * W + p / s % W];"),
+    "upsample_rounds_to_nearest": (
+        "y[(pl * Ho + p) * Wo + q] = x[(pl * H + p / s) * W + q / s];",
+        "y[(pl * Ho + p) * Wo + q] = x[(pl * H + (p + s / 2) / s % H) * W + (q + s / 2) / s % W];"),
+    "upsample_points_border_on_input": (
+        "sum += f[a * K + b] * plane[(su / s) * W + sv / s];",
+        "sum += f[a * K + b] * plane[(i / s + a - r < 0 ? 0 : su / s) * W + sv / s];"),
     "dense_grad_sign": (
         "sum += dy[((n * H + i) * W + j) * Co + o] * x[((n * H + si) * W + sj) * Ci + c];",
         "sum -= dy[((n * H + i) * W + j) * Co + o] * x[((n * H + si) * W + sj) * Ci + c];"),
