@@ -391,6 +391,67 @@ def compare_ragged(dev, iters):
             "y_dx_bitwise_equal_to_per_image_path": bool(same)}
 
 
+def compare_upsample(dev, iters):
+    """The paper's sharpening benchmark (Section 6.6) on a 4K image: nearest
+    upsampling by 2, 4 and 8, then its 3 x 3 Laplacian (8 surrounded by -1),
+    zero border, FP32.  Fused (one pass, the upsampled image never stored) vs
+    the two-call path (upsample, then filter), with the output bandwidth of
+    the fused pass against the measured HBM peak and sampled errors against
+    the FP64 oracle."""
+    import torch
+    import oracle
+    import workloads
+    from paper_2504_01266_gb300 import _lib as L
+    pk = peaks()
+    C, H, W = 3, 2160, 3840
+    g = torch.Generator().manual_seed(2504 + 6)
+    xh = torch.rand((1, C, H, W), generator=g)
+    lap = torch.tensor([[-1.0, -1, -1], [-1, 8, -1], [-1, -1, -1]]).repeat(C, 1, 1)
+    x, w = xh.to(dev), lap.to(dev)
+    stream = torch.cuda.current_stream(dev)
+    sp = stream.cuda_stream
+    d = L.desc(1, C, C, H, W, 3, C, 0, L.GIGA_F32, L.GIGA_LAYOUT_NCHW)
+    out = {"workload": "1x3x2160x3840 FP32 (a 4K RGB image), nearest upsampling by s, then "
+                       "the paper's 3x3 Laplacian, zero border",
+           "scales": {}}
+    for s in (2, 4, 8):
+        Ho, Wo = H * s, W * s
+        y = torch.empty((1, C, Ho, Wo), device=dev)
+        up = torch.empty_like(y)
+        dbig = L.desc(1, C, C, Ho, Wo, 3, C, 0, L.GIGA_F32, L.GIGA_LAYOUT_NCHW)
+
+        def fused():
+            L.check(L.giga_upsample_conv2d_fwd(d, s, x.data_ptr(), w.data_ptr(), y.data_ptr(),
+                                               sp), "upsample_conv2d")
+
+        def two_pass():
+            L.check(L.giga_upsample_nearest(d, s, x.data_ptr(), up.data_ptr(), sp), "upsample")
+            L.check(L.giga_conv2d_fwd(dbig, up.data_ptr(), w.data_ptr(), y.data_ptr(), None, 0,
+                                      sp), "fwd")
+
+        def up_only():
+            L.check(L.giga_upsample_nearest(d, s, x.data_ptr(), up.data_ptr(), sp), "upsample")
+        t_fused = _events(stream, fused, iters)
+        t_two = _events(stream, two_pass, iters)
+        t_up = _events(stream, up_only, iters)
+        fused()
+        px = C * Ho * Wo
+        bytes_fused = 4 * px + 4 * C * H * W   # write y, read x once
+        gbs = bytes_fused / (t_fused * 1e-3) / 1e9
+        idx = torch.unique(torch.cat([workloads.sample_indices(px, 1500, salt=s),
+                                      workloads.border_indices(1, C, Ho, Wo, 2, salt=s)]))
+        got = y.reshape(-1)[idx.to(dev)].double().cpu().numpy()
+        ref = oracle.upsample_dw_fwd_points(xh.numpy(), lap.numpy(), 0, s, idx.numpy())
+        out["scales"][str(s)] = {
+            "fused_ms": t_fused, "two_pass_ms": t_two, "upsample_only_ms": t_up,
+            "speedup": t_two / t_fused, "output_gpixel_s": px / (t_fused * 1e-3) / 1e9,
+            "fused_gbs": gbs, "fused_frac_of_hbm": gbs / pk["hbm_gbs"],
+            "err_normwise_sampled": _normwise(got, ref)}
+        del y, up
+        torch.cuda.empty_cache()
+    return out
+
+
 def compare_dense(dev, iters, bf16_peak):
     """Dense 3 x 3, 64 -> 64 channels, 8 x 1024 x 1024 BF16 NHWC on tcgen05:
     forward, input gradient and filter gradient, TFLOP/s against the measured
@@ -664,7 +725,8 @@ def run_giga(args):
         compare = {}
         for name, fn in (("bf16", lambda: compare_bf16(dev, 5)),
                          ("ragged", lambda: compare_ragged(dev, 5)),
-                         ("dense", lambda: compare_dense(dev, 10, bf16_peak))):
+                         ("dense", lambda: compare_dense(dev, 10, bf16_peak)),
+                         ("upsample_sharpen", lambda: compare_upsample(dev, 10))):
             compare[name] = fn()
             torch.cuda.empty_cache()
 
@@ -713,7 +775,8 @@ def run_section(args):
         pass
     fn = {"bf16": lambda: compare_bf16(dev, args.steps),
           "ragged": lambda: compare_ragged(dev, args.steps),
-          "dense": lambda: compare_dense(dev, args.steps, peak)}[args.section]
+          "dense": lambda: compare_dense(dev, args.steps, peak),
+          "upsample": lambda: compare_upsample(dev, args.steps)}[args.section]
     print(json.dumps({"section": args.section, "result": fn()}))
     return 0
 
@@ -735,7 +798,7 @@ def main():
                          "else tune and save the choices there")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the BF16 / ragged / dense comparison measurements")
-    ap.add_argument("--section", choices=["bf16", "ragged", "dense"],
+    ap.add_argument("--section", choices=["bf16", "ragged", "dense", "upsample"],
                     help="run only this comparison and print its result (profiling aid)")
     ap.add_argument("--images", type=int, default=N,
                     help="images per GPU (profiling runs use 1: 201 MB per tensor, above L2)")

@@ -175,6 +175,28 @@ giga_status_t giga_conv2d_batched_workspace_size(const giga_image_t* images, int
                                                  int32_t ops, size_t* bytes);
 
 /* ------------------------------------------------------------------------
+ * Upsampling (Section 4.2.3) and the sharpening benchmark (Section 6.6).
+ * desc describes the INPUT: NCHW, N x C_in x H x W, groups == C_in ==
+ * C_out, FP32 or BF16; the output y is N x C x (H * scale) x (W * scale) in
+ * the same type, device memory owned by the caller, not aliasing x.
+ *
+ * giga_upsample_nearest: nearest-neighbour upsampling by the integer factor
+ *   scale >= 1: y[n][c][p][q] = x[n][c][p / scale][q / scale] (integer
+ *   division; every pixel becomes a scale x scale block).  desc->K and
+ *   desc->border are checked but not used.
+ * giga_upsample_conv2d_fwd: the depthwise K x K filter w[C][K][K] (FP32,
+ *   odd K <= 15) applied to the upsampled image with desc->border on the
+ *   upsampled image, in one pass: the upsampled image is never stored.
+ *   Equal, bit for bit in FP32, to giga_upsample_nearest followed by
+ *   giga_conv2d_fwd on its output.
+ * Both are asynchronous on `stream`; GIGA_ERR_INVALID_ARG for scale < 1 or an
+ * upsampled side of 2^31 or more. */
+giga_status_t giga_upsample_nearest(const giga_conv2d_desc_t* desc, int32_t scale, const void* x,
+                                    void* y, void* stream);
+giga_status_t giga_upsample_conv2d_fwd(const giga_conv2d_desc_t* desc, int32_t scale,
+                                       const void* x, const void* w, void* y, void* stream);
+
+/* ------------------------------------------------------------------------
  * Autotuner.  Candidates: forward and input gradient (op 1 / 2): id 0..3 =
  * {8, 4} rows per thread (bit 0) x {one tile per CTA, persistent
  * double-buffered CTAs} (bit 1); filter gradient (op 4): id 0..4 = tiles

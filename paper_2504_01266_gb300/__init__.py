@@ -22,7 +22,7 @@ BORDERS = {"zero": _lib.GIGA_BORDER_ZERO, "clamp": _lib.GIGA_BORDER_CLAMP}
 DTYPES = {torch.float32: _lib.GIGA_F32, torch.bfloat16: _lib.GIGA_BF16}
 
 __all__ = ["conv2d", "conv2d_fwd", "conv2d_bwd", "conv2d_bwd_input", "conv2d_bwd_filter",
-           "DepthwiseConv2d", "workspace", "BORDERS"]
+           "DepthwiseConv2d", "workspace", "BORDERS", "upsample_nearest", "upsample_conv2d"]
 
 
 def _border(border) -> int:
@@ -79,6 +79,37 @@ def conv2d_fwd(x: torch.Tensor, w: torch.Tensor, border="zero", out=None) -> tor
     ws = workspace(d, _lib.GIGA_OP_FWD, x.device)
     _lib.check(_lib.giga_conv2d_fwd(d, _ptr(x), _ptr(w), _ptr(y), _ptr(ws), _nbytes(ws),
                                     _stream(x.device)), "giga_conv2d_fwd")
+    return y
+
+
+def _up_out(x: torch.Tensor, scale: int, out):
+    N, C, H, W = x.shape
+    shape = (N, C, H * scale, W * scale)
+    if out is None:
+        return torch.empty(shape, dtype=x.dtype, device=x.device)
+    if tuple(out.shape) != shape:
+        raise ValueError(f"out must have shape {shape}")
+    return out
+
+
+def upsample_nearest(x: torch.Tensor, scale: int, out=None) -> torch.Tensor:
+    """Nearest-neighbour upsampling by an integer factor (NCHW)."""
+    _require_cuda(x)
+    d = dw_desc(x, 1, "zero")
+    y = _up_out(x, scale, out)
+    _lib.check(_lib.giga_upsample_nearest(d, int(scale), _ptr(x), _ptr(y), _stream(x.device)),
+               "giga_upsample_nearest")
+    return y
+
+
+def upsample_conv2d(x: torch.Tensor, w: torch.Tensor, scale: int, border="zero",
+                    out=None) -> torch.Tensor:
+    """The depthwise filter applied to the upsampled image, in one pass."""
+    _require_cuda(x, w)
+    d = dw_desc(x, w.shape[-1], border)
+    y = _up_out(x, scale, out)
+    _lib.check(_lib.giga_upsample_conv2d_fwd(d, int(scale), _ptr(x), _ptr(w), _ptr(y),
+                                             _stream(x.device)), "giga_upsample_conv2d_fwd")
     return y
 
 

@@ -37,6 +37,7 @@ GIGA_OP_BWD_FILTER = 4
 EXPORTS = (
     "giga_conv2d_workspace_size", "giga_conv2d_fwd", "giga_conv2d_bwd_input",
     "giga_conv2d_bwd_filter", "giga_conv2d_bwd", "giga_conv2d_bwd_filter_noalloc",
+    "giga_upsample_nearest", "giga_upsample_conv2d_fwd",
     "giga_batched_plan_create",
     "giga_batched_plan_workspace_size", "giga_batched_plan_upload", "giga_batched_plan_run",
     "giga_batched_plan_destroy", "giga_conv2d_batched", "giga_conv2d_batched_workspace_size",
@@ -88,6 +89,8 @@ _SIGS = {
     "giga_conv2d_bwd_filter": (_ST, [_DESC, _P, _P, _P, _P, _SZ, _P]),
     "giga_conv2d_bwd": (_ST, [_DESC, _P, _P, _P, _P, _P, _P, _SZ, _P]),
     "giga_conv2d_bwd_filter_noalloc": (_ST, [_DESC, _P, _P, _P, _P]),
+    "giga_upsample_nearest": (_ST, [_DESC, _I32, _P, _P, _P]),
+    "giga_upsample_conv2d_fwd": (_ST, [_DESC, _I32, _P, _P, _P, _P]),
     "giga_batched_plan_create": (_ST, [_IMG, _I32, _I32, _I32, _I32, ctypes.POINTER(_P)]),
     "giga_batched_plan_workspace_size": (_ST, [_P, ctypes.POINTER(_SZ)]),
     "giga_batched_plan_upload": (_ST, [_P, _P, _SZ, _P]),
@@ -177,6 +180,14 @@ def giga_conv2d_bwd_filter_noalloc(d, x, dy, dw, stream) -> int:
 
 def giga_conv2d_bwd(d, x, dy, w, dx, dw, ws, ws_bytes, stream) -> int:
     return load().giga_conv2d_bwd(ctypes.byref(d), x, dy, w, dx, dw, ws, ws_bytes, stream)
+
+
+def giga_upsample_nearest(d, scale, x, y, stream) -> int:
+    return load().giga_upsample_nearest(ctypes.byref(d), scale, x, y, stream)
+
+
+def giga_upsample_conv2d_fwd(d, scale, x, w, y, stream) -> int:
+    return load().giga_upsample_conv2d_fwd(ctypes.byref(d), scale, x, w, y, stream)
 
 
 def giga_batched_plan_create(images, n, ops, border, dtype):

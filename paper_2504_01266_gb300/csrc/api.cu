@@ -308,6 +308,76 @@ giga_status_t giga_conv2d_fwd(const giga_conv2d_desc_t* desc, const void* x, con
   return run_tuned(TUNE_FWD, a, static_cast<cudaStream_t>(stream));
 }
 
+// Shared checks of the two upsampling entry points; fills a.
+static giga_status_t up_prepare(const giga_conv2d_desc_t* desc, int32_t scale, const void* x,
+                                const void* y, UpArgs& a) {
+  giga_status_t s = check_desc(desc);
+  if (s != GIGA_OK) return s;
+  if (!is_depthwise(desc))
+    return fail(GIGA_ERR_UNSUPPORTED, "upsampling takes depthwise (per-channel) NCHW tensors");
+  if (scale < 1) return fail(GIGA_ERR_INVALID_ARG, "scale must be >= 1, got " + std::to_string(scale));
+  const int64_t Ho = desc->H * scale, Wo = desc->W * scale;
+  if (Ho >= (1LL << 31) || Wo >= (1LL << 31) || Ho * Wo >= (1LL << 40))
+    return fail(GIGA_ERR_INVALID_ARG, "upsampled image too large");
+  const size_t es = elem_size(desc->dtype);
+  const size_t n_in = (size_t)dw_numel(desc), n_out = (size_t)(dw_planes(desc) * Ho * Wo);
+  if ((s = check_ptr(x, n_in, es, "x")) || (s = check_ptr(y, n_out, es, "y"))) return s;
+  if (n_out && n_in && (reinterpret_cast<uintptr_t>(x) < reinterpret_cast<uintptr_t>(y) + n_out * es) &&
+      (reinterpret_cast<uintptr_t>(y) < reinterpret_cast<uintptr_t>(x) + n_in * es))
+    return fail(GIGA_ERR_INVALID_ARG, "y aliases x");
+  std::memset(&a, 0, sizeof(a));
+  a.x = x;
+  a.y = const_cast<void*>(y);
+  a.N = desc->N;
+  a.C = desc->C_in;
+  a.H = desc->H;
+  a.W = desc->W;
+  a.Ho = Ho;
+  a.Wo = Wo;
+  a.s = scale;
+  a.K = desc->K;
+  a.border = desc->border;
+  a.dtype = desc->dtype;
+  const uintptr_t align = desc->dtype == GIGA_F32 ? 16 : 8;
+  a.vec = (Wo % 4 == 0 && reinterpret_cast<uintptr_t>(y) % align == 0) ? 1 : 0;
+  return GIGA_OK;
+}
+
+giga_status_t giga_upsample_nearest(const giga_conv2d_desc_t* desc, int32_t scale, const void* x,
+                                    void* y, void* stream) {
+  clear_error();
+  UpArgs a;
+  giga_status_t s = up_prepare(desc, scale, x, y, a);
+  if (s != GIGA_OK) return s;
+  if (a.N * a.C * a.Ho * a.Wo == 0) return GIGA_OK;
+  cudaError_t e = up_nearest_launch(a, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? GIGA_OK : cuda_fail(e, "upsample launch");
+}
+
+giga_status_t giga_upsample_conv2d_fwd(const giga_conv2d_desc_t* desc, int32_t scale,
+                                       const void* x, const void* w, void* y, void* stream) {
+  clear_error();
+  UpArgs a;
+  giga_status_t s = up_prepare(desc, scale, x, y, a);
+  if (s != GIGA_OK) return s;
+  if (desc->K > kMaxKFilter)
+    return fail(GIGA_ERR_UNSUPPORTED, "upsample-then-filter supports K <= 15");
+  const size_t n_out = (size_t)(a.N * a.C * a.Ho * a.Wo);
+  if ((s = check_ptr(w, n_out ? (size_t)desc->C_in * desc->K * desc->K : 0, 4, "w"))) return s;
+  if (n_out == 0) return GIGA_OK;
+  if (scale == 1) {  // no upsampling: the plain depthwise forward, bit for bit
+    DwArgs d = make_args(desc);
+    d.x = x;
+    d.y = y;
+    d.w = static_cast<const float*>(w);
+    d.vec = vec_ok(d, x, y, nullptr);
+    return run_tuned(TUNE_FWD, d, static_cast<cudaStream_t>(stream));
+  }
+  a.w = static_cast<const float*>(w);
+  cudaError_t e = up_fwd_launch(a, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? GIGA_OK : cuda_fail(e, "upsample-then-filter launch");
+}
+
 giga_status_t giga_conv2d_bwd_input(const giga_conv2d_desc_t* desc, const void* dy,
                                     const void* w, void* dx, void* ws, size_t ws_bytes,
                                     void* stream) {

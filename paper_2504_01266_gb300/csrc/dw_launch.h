@@ -28,6 +28,18 @@ cudaError_t dw_bwd_launch(const DwArgs& a, const DwConfig& cfg, cudaStream_t st)
 template <int K>
 cudaError_t dw_filter_launch(const DwArgs& a, const DwConfig& cfg, cudaStream_t st);
 
+// Upsampling by an integer factor s, alone or followed by the depthwise
+// filter (upsample.cu).  N, C, H, W: the input; Ho = H * s, Wo = W * s.
+struct UpArgs {
+  const void* x;
+  const float* w;
+  void* y;
+  int64_t N, C, H, W, Ho, Wo;
+  int s, K, border, dtype, vec;
+};
+cudaError_t up_nearest_launch(const UpArgs& a, cudaStream_t st);
+cudaError_t up_fwd_launch(const UpArgs& a, cudaStream_t st);
+
 // Device error word of the depthwise kernels (nonzero after a bounded wait
 // gave up) for the current device; nullptr if unavailable.
 int* dw_error_word();

@@ -1,0 +1,329 @@
+// upsample.cu -- nearest-neighbour upsampling by an integer factor s (the
+// GigaAPI paper, Section 4.2.3) and the paper's sharpening benchmark fused
+// into one pass (Section 6.6): the K x K depthwise filter applied to the
+// upsampled image, whose pixels are read straight from the small input while
+// a tile is staged, so the upsampled image never goes to HBM.
+//
+//   up[n][c][p][q] = x[n][c][p / s][q / s]                      (integer division)
+//   y[n][c][p][q]  = sum_{a,b} w[c][a][b] * up~[n][c][p + a - r][q + b - r]
+//
+// up~ applies the border rule on the (H*s) x (W*s) upsampled image.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "dw_kernels.cuh"
+#include "dw_launch.h"
+
+namespace giga {
+
+// Unsigned division by a fixed divisor d >= 1 as a multiply-high and a shift
+// (round-up reciprocal; exact for every n < 2^31).
+struct FastDiv {
+  uint32_t mul, shift, d;
+};
+
+static FastDiv make_fastdiv(uint32_t d) {
+  FastDiv f{0, 0, d};
+  if (d == 1) return f;
+  uint32_t l = 0;
+  while ((1u << l) < d) ++l;
+  f.shift = l - 1;
+  f.mul = (uint32_t)((((uint64_t)1 << (32 + f.shift)) + d - 1) / d);
+  return f;
+}
+
+__device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv& f) {
+  return f.d == 1 ? n : (__umulhi(n, f.mul) >> f.shift);
+}
+
+// --------------------------------------------------------------- upsample
+// One thread per 4 consecutive outputs of a row (a 16/8-byte store when the
+// row allows it).  The chunk index splits into (row, chunk of row) by a
+// fixed-divisor division; the 4 source columns follow q0 / s incrementally.
+template <typename T>
+__global__ void __launch_bounds__(256) up_nearest_kernel(const T* __restrict__ x,
+                                                         T* __restrict__ y, int H, int W,
+                                                         int Ho, int Wo, FastDiv fs,
+                                                         FastDiv fcpr, FastDiv fho,
+                                                         uint32_t chunks, int vec) {
+  const uint32_t cpr = fcpr.d;
+  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < chunks;
+       k += gridDim.x * blockDim.x) {
+    const uint32_t row = fdiv(k, fcpr);  // plane * Ho + p
+    const int q0 = (int)(k - row * cpr) * 4;
+    const uint32_t plane = fdiv(row, fho);
+    const int p = (int)(row - plane * (uint32_t)Ho);
+    const T* src = x + ((int64_t)plane * H + fdiv((uint32_t)p, fs)) * (int64_t)W;
+    T* dst = y + (int64_t)row * Wo + q0;
+    int sv = (int)fdiv((uint32_t)q0, fs), rem = q0 - sv * fs.d;
+    float e[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      e[q] = q0 + q < Wo ? Elem<T>::load(src + sv) : 0.f;
+      if (++rem == (int)fs.d) {
+        rem = 0;
+        ++sv;
+      }
+    }
+    if (vec && q0 + 3 < Wo) {
+      Elem<T>::store4(dst, make_float4(e[0], e[1], e[2], e[3]));
+    } else {
+      for (int q = 0; q < 4 && q0 + q < Wo; ++q) Elem<T>::store(dst + q, e[q]);
+    }
+  }
+}
+
+// ------------------------------------------------- upsample, then filter
+// One 64 x 128 output tile of the upsampled grid per CTA (8 warps, 8 rows
+// each), scale s >= 2 (scale 1 is the plain forward).  The input pixels the
+// halo tile needs -- rows and columns of the upsampled window divided by s,
+// clamped to the image -- are first copied to shared memory; then every
+// shared cell (sr, sc) of the FP32 halo tile, upsampled pixel
+// (u, v) = (ty0 - r + sr, tx0 - RP + sc), takes the border rule on the
+// upsampled image (zero: the cell is 0; clamp: (u, v) clamped) and reads the
+// copied input pixel (u / s, v / s).  The forward loop and the store are the
+// depthwise forward's.
+template <int K>
+struct UpShape {
+  using G = Geo<K>;
+  static constexpr int TH = kWarps * 8;
+  static constexpr int ROWS = TH + 2 * G::R;
+  static constexpr int SRC_ROWS = ROWS / 2 + 2;                // input rows under the window (s >= 2)
+  static constexpr int SRC_COLS = round_up(G::SP / 2 + 2, 4);  // input columns (pitch)
+  static constexpr int STAGE = round_up(G::WPAD, 4) + SRC_ROWS * SRC_COLS;  // filter + pixels
+  static constexpr int TABLES = G::SP + 2 * round_up(ROWS, 4);  // column map, row tables
+  static constexpr int SM_FLOATS_1 = ROWS * G::SP + TABLES + STAGE;  // one tile per CTA
+  static constexpr int SM_FLOATS = SM_FLOATS_1 + STAGE;               // two stages
+};
+
+// One 64 x 128 output tile of the upsampled grid at a time per CTA (8 warps,
+// 8 rows each), over tiles t = blockIdx.x, + gridDim.x, ... (launched with one
+// tile per CTA: measured faster than persistent CTAs, which need a second
+// stage); scale s >= 2 (scale 1 is the plain forward).  Per tile: the input pixels
+// its halo window needs (rows and columns of the upsampled window divided by
+// s, clamped to the image) and its plane's filter are copied to one of two
+// stages -- those of the next tile are copied while this one is computed --
+// then every shared cell (sr, sc) of the FP32 halo tile, upsampled pixel
+// (u, v) = (ty0 - r + sr, tx0 - RP + sc), takes the border rule on the
+// upsampled image (zero: the cell is 0; clamp: (u, v) clamped) and reads the
+// copied input pixel (u / s, v / s).  The forward loop and the store are the
+// depthwise forward's.
+template <typename T, int K>
+__global__ void __launch_bounds__(kThreads) up_fwd_kernel(const T* __restrict__ x,
+                                                          const float* __restrict__ w,
+                                                          T* __restrict__ y, int C, int H, int W,
+                                                          int Ho, int Wo, FastDiv fs, int tiles_x,
+                                                          int tiles_y, int64_t num_tiles,
+                                                          int clamp, int vec) {
+  using G = Geo<K>;
+  using U = UpShape<K>;
+  constexpr int PY = 8;
+  extern __shared__ __align__(16) float smem[];
+  float* st = smem;                                 // ROWS x SP halo tile
+  int* scol = reinterpret_cast<int*>(st + U::ROWS * G::SP);  // SP column map
+  int* srow_of = scol + G::SP;                      // ROWS: input row of each halo row
+  int* slead = srow_of + round_up(U::ROWS, 4);      // ROWS: first row of its run
+  // 1 or 2 x {filter, SRC_ROWS x SRC_COLS pixels}; the second only when a CTA
+  // runs several tiles
+  float* stages = reinterpret_cast<float*>(scol) + U::TABLES;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  struct Tile {
+    int ty0, tx0, su0, sv0, nr, nc;
+    int64_t plane;
+  };
+  auto locate = [&](int64_t t) {
+    Tile tl;
+    tl.tx0 = (int)(t % tiles_x) * kTileW;
+    const int64_t t2 = t / tiles_x;
+    tl.ty0 = (int)(t2 % tiles_y) * U::TH;
+    tl.plane = t2 / tiles_y;
+    // input window: upsampled rows [ty0 - r, ty0 + TH + r), columns
+    // [tx0 - RP, tx0 + 128 + RP), clamped to the upsampled image, divided by s
+    const int u_lo = max(tl.ty0 - G::R, 0), u_hi = min(tl.ty0 + U::TH + G::R, Ho) - 1;
+    const int v_lo = max(tl.tx0 - G::RP, 0), v_hi = min(tl.tx0 + kTileW + G::RP, Wo) - 1;
+    tl.su0 = (int)fdiv((uint32_t)u_lo, fs);
+    tl.sv0 = (int)fdiv((uint32_t)v_lo, fs);
+    tl.nr = (int)fdiv((uint32_t)u_hi, fs) - tl.su0 + 1;  // <= SRC_ROWS
+    tl.nc = (int)fdiv((uint32_t)v_hi, fs) - tl.sv0 + 1;  // <= SRC_COLS
+    return tl;
+  };
+  // copy tile tl's filter and input pixels to stage b, every copy in flight
+  // at once (FP32: 4-byte cp.async; BF16: loads issued before the widened
+  // stores); one commit group per stage
+  auto stage = [&](const Tile& tl, int b) {
+    float* sw = stages + b * U::STAGE;
+    float* ss = sw + round_up(G::WPAD, 4);
+    stage_filter_async<K>(sw, w + (int64_t)(tl.plane % C) * K * K, false, kThreads);
+    const T* xp = x + tl.plane * (int64_t)H * W;
+    const int n = tl.nr * tl.nc;
+    if constexpr (sizeof(T) == 4) {
+      for (int k = threadIdx.x; k < n; k += kThreads) {
+        const int r = k / tl.nc, c = k - (k / tl.nc) * tl.nc;
+        cp_async4(ss + r * U::SRC_COLS + c, xp + (int64_t)(tl.su0 + r) * W + tl.sv0 + c, true);
+      }
+    } else {
+      constexpr int PER = (U::SRC_ROWS * U::SRC_COLS + kThreads - 1) / kThreads;
+      float v[PER];
+#pragma unroll
+      for (int i = 0; i < PER; ++i) {
+        const int k = i * kThreads + threadIdx.x;
+        if (k < n) {
+          const int r = k / tl.nc, c = k - (k / tl.nc) * tl.nc;
+          v[i] = Elem<T>::load(xp + (int64_t)(tl.su0 + r) * W + tl.sv0 + c);
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < PER; ++i) {
+        const int k = i * kThreads + threadIdx.x;
+        if (k < n) ss[(k / tl.nc) * U::SRC_COLS + (k - (k / tl.nc) * tl.nc)] = v[i];
+      }
+    }
+    cp_async_commit();
+  };
+
+  int64_t t = blockIdx.x;
+  if (t >= num_tiles) return;
+  Tile cur = locate(t);
+  stage(cur, 0);
+  for (int b = 0; t < num_tiles; t += gridDim.x, b ^= 1) {
+    const int64_t tn = t + gridDim.x;
+    Tile nxt;
+    if (tn < num_tiles) {
+      nxt = locate(tn);
+      stage(nxt, b ^ 1);  // that stage was last read before the previous tile's barriers
+      cp_async_wait_group<1>();
+    } else {
+      cp_async_wait_group<0>();
+    }
+    const float* sw = stages + b * U::STAGE;
+    const float* ss = sw + round_up(G::WPAD, 4);
+    // Expand.  The column mapping is the same for every row: scol[sc] is the
+    // copied input column of halo column sc (-1: zero border, outside).  Halo
+    // rows come in runs that read the same input row (srow_of; -1: zero
+    // border, outside): the first row of a run (slead) is built from the
+    // copied pixels, the others copy it.
+    const int ty0 = cur.ty0, tx0 = cur.tx0, su0 = cur.su0, sv0 = cur.sv0;
+    auto src_row = [&](int sr) {
+      int u = ty0 - G::R + sr;
+      if (u < 0 || u >= Ho) {
+        if (!clamp) return -1;
+        u = u < 0 ? 0 : Ho - 1;
+      }
+      return (int)fdiv((uint32_t)u, fs) - su0;
+    };
+    for (int sc = threadIdx.x; sc < G::SP; sc += kThreads) {
+      int v = tx0 - G::RP + sc;
+      int m = -1;
+      if (clamp || (v >= 0 && v < Wo)) {
+        v = v < 0 ? 0 : (v >= Wo ? Wo - 1 : v);
+        m = (int)fdiv((uint32_t)v, fs) - sv0;
+      }
+      scol[sc] = m;
+    }
+    for (int sr = threadIdx.x; sr < U::ROWS; sr += kThreads) {
+      const int j = src_row(sr);
+      int lead = sr;
+      while (lead > 0 && src_row(lead - 1) == j) --lead;
+      srow_of[sr] = j;
+      slead[sr] = lead;
+    }
+    cta_barrier();  // copies of this tile landed; tables ready
+    constexpr int CPR = G::SP / 4;
+    for (int k = threadIdx.x; k < U::ROWS * CPR; k += kThreads) {
+      const int sr = k / CPR, sc = (k - (k / CPR) * CPR) * 4;
+      if (slead[sr] != sr) continue;
+      const int j = srow_of[sr];
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (j >= 0) {
+        const int4 m = *reinterpret_cast<const int4*>(scol + sc);
+        const float* srow = ss + j * U::SRC_COLS;
+        v.x = m.x >= 0 ? srow[m.x] : 0.f;
+        v.y = m.y >= 0 ? srow[m.y] : 0.f;
+        v.z = m.z >= 0 ? srow[m.z] : 0.f;
+        v.w = m.w >= 0 ? srow[m.w] : 0.f;
+      }
+      *reinterpret_cast<float4*>(st + sr * G::SP + sc) = v;
+    }
+    cta_barrier();
+    for (int k = threadIdx.x; k < U::ROWS * CPR; k += kThreads) {
+      const int sr = k / CPR, sc = (k - (k / CPR) * CPR) * 4;
+      const int lead = slead[sr];
+      if (lead != sr)
+        *reinterpret_cast<float4*>(st + sr * G::SP + sc) =
+            *reinterpret_cast<const float4*>(st + lead * G::SP + sc);
+    }
+    cta_barrier();
+    float acc[PY][4];
+    fwd_block<K, PY, float>(st + warp * PY * G::SP + 4 * lane, sw, acc);
+    store_block<T, PY>(y + cur.plane * (int64_t)Ho * Wo, Ho, Wo, ty0 + warp * PY,
+                       tx0 + 4 * lane, vec != 0, acc);
+    cta_barrier();  // the halo tile, tables and stage b are free again
+    cur = nxt;
+  }
+}
+
+template <typename T, int K>
+static cudaError_t up_fwd_impl(const UpArgs& a, cudaStream_t st) {
+  using U = UpShape<K>;
+  const size_t smem = (size_t)U::SM_FLOATS * 4;
+  auto kern = up_fwd_kernel<T, K>;
+  cudaError_t e = set_smem_once<up_fwd_kernel<T, K>>(smem);
+  if (e != cudaSuccess) return e;
+  const int64_t tiles_x = (a.Wo + kTileW - 1) / kTileW;
+  const int64_t tiles_y = (a.Ho + U::TH - 1) / U::TH;
+  const int64_t tiles = a.N * a.C * tiles_x * tiles_y;
+  if (tiles > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  const int64_t grid = tiles;  // one tile per CTA: the second stage is never used
+  const size_t smem1 = (size_t)U::SM_FLOATS_1 * 4;
+  kern<<<(unsigned)grid, kThreads, smem1, st>>>(
+      static_cast<const T*>(a.x), a.w, static_cast<T*>(a.y), (int)a.C, (int)a.H, (int)a.W,
+      (int)a.Ho, (int)a.Wo, make_fastdiv((uint32_t)a.s), (int)tiles_x, (int)tiles_y, tiles,
+      a.border, a.vec);
+  note_launch();
+  return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t up_fwd_dispatch(const UpArgs& a, cudaStream_t st) {
+  switch (a.K) {
+    case 1: return up_fwd_impl<T, 1>(a, st);
+    case 3: return up_fwd_impl<T, 3>(a, st);
+    case 5: return up_fwd_impl<T, 5>(a, st);
+    case 7: return up_fwd_impl<T, 7>(a, st);
+    case 9: return up_fwd_impl<T, 9>(a, st);
+    case 11: return up_fwd_impl<T, 11>(a, st);
+    case 13: return up_fwd_impl<T, 13>(a, st);
+    case 15: return up_fwd_impl<T, 15>(a, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t up_fwd_launch(const UpArgs& a, cudaStream_t st) {
+  return a.dtype == 0 ? up_fwd_dispatch<float>(a, st) : up_fwd_dispatch<__nv_bfloat16>(a, st);
+}
+
+cudaError_t up_nearest_launch(const UpArgs& a, cudaStream_t st) {
+  const int64_t cpr = (a.Wo + 3) / 4;
+  const int64_t chunks = a.N * a.C * a.Ho * cpr;
+  if (chunks >= (1LL << 32) || a.N * a.C * a.Ho >= (1LL << 32)) return cudaErrorInvalidValue;
+  const int64_t want = (chunks + 255) / 256;
+  const int grid = (int)std::min<int64_t>(want, (int64_t)sm_count() * 16);
+  const FastDiv fs = make_fastdiv((uint32_t)a.s), fc = make_fastdiv((uint32_t)cpr),
+                fh = make_fastdiv((uint32_t)a.Ho);
+  if (a.dtype == 0)
+    up_nearest_kernel<float><<<grid, 256, 0, st>>>(static_cast<const float*>(a.x),
+                                                   static_cast<float*>(a.y), (int)a.H, (int)a.W,
+                                                   (int)a.Ho, (int)a.Wo, fs, fc, fh,
+                                                   (uint32_t)chunks, a.vec);
+  else
+    up_nearest_kernel<__nv_bfloat16><<<grid, 256, 0, st>>>(
+        static_cast<const __nv_bfloat16*>(a.x), static_cast<__nv_bfloat16*>(a.y), (int)a.H,
+        (int)a.W, (int)a.Ho, (int)a.Wo, fs, fc, fh, (uint32_t)chunks, a.vec);
+  note_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace giga
