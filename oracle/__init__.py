@@ -336,3 +336,16 @@ def upsample_dw_fwd_points(x, w, border: int, s: int, idx) -> np.ndarray:
                                                  _pi(idx), idx.size, _p(out)),
            "upsample_dw_fwd_points")
     return out
+
+
+# --------------------------------------------------------- separable filters
+
+def dw_fwd_separable(x, wcol, wrow, border: int) -> np.ndarray:
+    """The depthwise filter whose taps are w[c][a][b] = wcol[c][a] * wrow[c][b]
+    (the outer product, formed in FP64), applied by the plain definition
+    ``dw_fwd``: filtering with a separable filter is the same neighbourhood
+    sum as with its full K x K form."""
+    wc, wr = _f64(wcol), _f64(wrow)
+    if wc.ndim != 2 or wc.shape != wr.shape:
+        raise ValueError("wcol and wrow must both be (C, K)")
+    return dw_fwd(x, wc[:, :, None] * wr[:, None, :], border)

@@ -365,10 +365,33 @@ def pin_upsample_sharpen():
     assert np.all(oracle.upsample_dw_fwd(const, lap, CLAMP, 4) == 0.0)
 
 
+def pin_separable_filter():
+    """A separable filter (column filter times row filter, both asymmetric and
+    different) equals a row-only pass followed by a column-only pass, for both
+    borders, and torch's FP64 convolution with the K x 1 then 1 x K kernels
+    (zero border) -- which also fixes which factor runs along which axis."""
+    g = rng(23)
+    for K in (3, 5, 9):
+        r = K // 2
+        wc = g.standard_normal((2, K))
+        wr = g.standard_normal((2, K))
+        x = g.standard_normal((2, 2, 11, 13))
+        rowf = np.zeros((2, K, K)); rowf[:, r, :] = wr
+        colf = np.zeros((2, K, K)); colf[:, :, r] = wc
+        for border in (ZERO, CLAMP):
+            two = oracle.dw_fwd(oracle.dw_fwd(x, rowf, border), colf, border)
+            assert rel(oracle.dw_fwd_separable(x, wc, wr, border), two) < 1e-13, (K, border)
+        xt = torch.from_numpy(x)
+        t = F.conv2d(xt, torch.from_numpy(wc)[:, None, :, None], padding=(r, 0), groups=2)
+        t = F.conv2d(t, torch.from_numpy(wr)[:, None, None, :], padding=(0, r), groups=2)
+        assert rel(oracle.dw_fwd_separable(x, wc, wr, ZERO), t.numpy()) < 1e-13, K
+        assert rel(oracle.dw_fwd_separable(x, wr, wc, ZERO), t.numpy()) > 1e-3, K
+
+
 PINS = [pin_golden, pin_delta, pin_shift, pin_box_constant, pin_torch_crosscheck,
         pin_separable_gaussian, pin_linearity, pin_translation, pin_operator_bruteforce,
         pin_adjoint, pin_filter_bilinear, pin_finite_differences, pin_points_match_full,
-        pin_dense, pin_upsample_nearest, pin_upsample_sharpen]
+        pin_dense, pin_upsample_nearest, pin_upsample_sharpen, pin_separable_filter]
 
 
 @pytest.mark.parametrize("pin", PINS, ids=[p.__name__ for p in PINS])
