@@ -452,6 +452,57 @@ def compare_upsample(dev, iters):
     return out
 
 
+def compare_separable(dev, iters):
+    """Separable filters (Gaussians, sigma = K / 6) on the benchmark images
+    (8 x 3 x 4096 x 4096 FP32, clamp): the row-then-column path vs the general
+    K x K forward on the same outer-product filter, with the separable path's
+    HBM fraction (8 bytes per pixel) and sampled errors against the oracle."""
+    import torch
+    import numpy as np
+    import oracle
+    import workloads
+    from paper_2504_01266_gb300 import _lib as L
+    pk = peaks()
+    x, _ = workloads.plain_scale(3)
+    xd = x.to(dev)
+    y = torch.empty_like(xd)
+    Nn, Cc, Hh, Ww = x.shape
+    stream = torch.cuda.current_stream(dev)
+    sp = stream.cuda_stream
+    out = {"workload": "8x3x4096x4096 FP32 U[0,1), Gaussian filters sigma = K/6 (row and "
+                       "column factors), clamp border", "K": {}}
+    for K in (3, 7, 15):
+        r = K // 2
+        t = np.exp(-np.arange(-r, r + 1) ** 2 / (2.0 * (K / 6.0) ** 2))
+        t = (t / t.sum()).astype(np.float32)
+        f = torch.from_numpy(np.repeat(t[None], Cc, 0)).to(dev)
+        wfull = (f[:, :, None] * f[:, None, :]).contiguous()
+        d = L.desc(Nn, Cc, Cc, Hh, Ww, K, Cc, 1, L.GIGA_F32, L.GIGA_LAYOUT_NCHW)
+
+        def sep():
+            L.check(L.giga_conv2d_fwd_separable(d, xd.data_ptr(), f.data_ptr(), f.data_ptr(),
+                                                y.data_ptr(), sp), "separable")
+
+        def full():
+            L.check(L.giga_conv2d_fwd(d, xd.data_ptr(), wfull.data_ptr(), y.data_ptr(), None, 0,
+                                      sp), "fwd")
+        t_full = _events(stream, full, iters)
+        t_sep = _events(stream, sep, iters)
+        sep()
+        idx = workloads.sample_indices(x.numel(), 1500, salt=70 + K)
+        got = y.reshape(-1)[idx.to(dev)].double().cpu().numpy()
+        ref = oracle.dw_fwd_points(x.numpy(), (np.outer(t, t)[None].repeat(Cc, 0)).astype(np.float64),
+                                   1, idx.numpy())
+        gbs = 8 * x.numel() / (t_sep * 1e-3) / 1e9
+        out["K"][str(K)] = {"separable_ms": t_sep, "full_ms": t_full, "speedup": t_full / t_sep,
+                            "separable_gbs": gbs, "separable_frac_of_hbm": gbs / pk["hbm_gbs"],
+                            "gpixel_tap_s": x.numel() * K * K / (t_sep * 1e-3) / 1e9,
+                            "err_normwise_sampled": _normwise(got, ref)}
+    del xd, y
+    torch.cuda.empty_cache()
+    return out
+
+
 def compare_dense(dev, iters, bf16_peak):
     """Dense 3 x 3, 64 -> 64 channels, 8 x 1024 x 1024 BF16 NHWC on tcgen05:
     forward, input gradient and filter gradient, TFLOP/s against the measured
@@ -726,7 +777,8 @@ def run_giga(args):
         for name, fn in (("bf16", lambda: compare_bf16(dev, 5)),
                          ("ragged", lambda: compare_ragged(dev, 5)),
                          ("dense", lambda: compare_dense(dev, 10, bf16_peak)),
-                         ("upsample_sharpen", lambda: compare_upsample(dev, 10))):
+                         ("upsample_sharpen", lambda: compare_upsample(dev, 10)),
+                         ("separable", lambda: compare_separable(dev, 10))):
             compare[name] = fn()
             torch.cuda.empty_cache()
 
@@ -776,7 +828,8 @@ def run_section(args):
     fn = {"bf16": lambda: compare_bf16(dev, args.steps),
           "ragged": lambda: compare_ragged(dev, args.steps),
           "dense": lambda: compare_dense(dev, args.steps, peak),
-          "upsample": lambda: compare_upsample(dev, args.steps)}[args.section]
+          "upsample": lambda: compare_upsample(dev, args.steps),
+          "separable": lambda: compare_separable(dev, args.steps)}[args.section]
     print(json.dumps({"section": args.section, "result": fn()}))
     return 0
 
@@ -798,7 +851,7 @@ def main():
                          "else tune and save the choices there")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the BF16 / ragged / dense comparison measurements")
-    ap.add_argument("--section", choices=["bf16", "ragged", "dense", "upsample"],
+    ap.add_argument("--section", choices=["bf16", "ragged", "dense", "upsample", "separable"],
                     help="run only this comparison and print its result (profiling aid)")
     ap.add_argument("--images", type=int, default=N,
                     help="images per GPU (profiling runs use 1: 201 MB per tensor, above L2)")

@@ -174,6 +174,17 @@ giga_status_t giga_conv2d_batched(const giga_image_t* images, int32_t n, int32_t
 giga_status_t giga_conv2d_batched_workspace_size(const giga_image_t* images, int32_t n,
                                                  int32_t ops, size_t* bytes);
 
+/* Separable depthwise filter: the K x K filter whose taps are
+ * w[c][a][b] = wcol[c][a] * wrow[c][b] (wcol, wrow FP32 [C][K]), e.g. a
+ * Gaussian or a box filter, applied as a row pass then a column pass in one
+ * launch: 2K instead of K^2 multiply-adds per pixel.  Same tensors, layout,
+ * borders and K range as giga_conv2d_fwd; the result equals giga_conv2d_fwd
+ * with the outer-product filter up to rounding order (FP32 accumulation in
+ * both passes).  Asynchronous on `stream`. */
+giga_status_t giga_conv2d_fwd_separable(const giga_conv2d_desc_t* desc, const void* x,
+                                        const float* wcol, const float* wrow, void* y,
+                                        void* stream);
+
 /* ------------------------------------------------------------------------
  * Upsampling (Section 4.2.3) and the sharpening benchmark (Section 6.6).
  * desc describes the INPUT: NCHW, N x C_in x H x W, groups == C_in ==

@@ -22,7 +22,8 @@ BORDERS = {"zero": _lib.GIGA_BORDER_ZERO, "clamp": _lib.GIGA_BORDER_CLAMP}
 DTYPES = {torch.float32: _lib.GIGA_F32, torch.bfloat16: _lib.GIGA_BF16}
 
 __all__ = ["conv2d", "conv2d_fwd", "conv2d_bwd", "conv2d_bwd_input", "conv2d_bwd_filter",
-           "DepthwiseConv2d", "workspace", "BORDERS", "upsample_nearest", "upsample_conv2d"]
+           "DepthwiseConv2d", "workspace", "BORDERS", "upsample_nearest", "upsample_conv2d",
+           "conv2d_separable"]
 
 
 def _border(border) -> int:
@@ -79,6 +80,18 @@ def conv2d_fwd(x: torch.Tensor, w: torch.Tensor, border="zero", out=None) -> tor
     ws = workspace(d, _lib.GIGA_OP_FWD, x.device)
     _lib.check(_lib.giga_conv2d_fwd(d, _ptr(x), _ptr(w), _ptr(y), _ptr(ws), _nbytes(ws),
                                     _stream(x.device)), "giga_conv2d_fwd")
+    return y
+
+
+def conv2d_separable(x: torch.Tensor, wcol: torch.Tensor, wrow: torch.Tensor, border="zero",
+                     out=None) -> torch.Tensor:
+    """y = K_w x for the separable filter w[c] = outer(wcol[c], wrow[c]) (both
+    (C, K) FP32): a row pass then a column pass, 2K multiply-adds per pixel."""
+    _require_cuda(x, wcol, wrow)
+    d = dw_desc(x, wcol.shape[-1], border)
+    y = torch.empty_like(x) if out is None else out
+    _lib.check(_lib.giga_conv2d_fwd_separable(d, _ptr(x), _ptr(wcol), _ptr(wrow), _ptr(y),
+                                              _stream(x.device)), "giga_conv2d_fwd_separable")
     return y
 
 

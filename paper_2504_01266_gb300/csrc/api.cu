@@ -308,6 +308,32 @@ giga_status_t giga_conv2d_fwd(const giga_conv2d_desc_t* desc, const void* x, con
   return run_tuned(TUNE_FWD, a, static_cast<cudaStream_t>(stream));
 }
 
+giga_status_t giga_conv2d_fwd_separable(const giga_conv2d_desc_t* desc, const void* x,
+                                        const float* wcol, const float* wrow, void* y,
+                                        void* stream) {
+  clear_error();
+  giga_status_t s = check_desc(desc);
+  if (s != GIGA_OK) return s;
+  if (!is_depthwise(desc))
+    return fail(GIGA_ERR_UNSUPPORTED, "separable filters are depthwise (groups == C_in == C_out)");
+  const size_t es = elem_size(desc->dtype);
+  const size_t n = (size_t)dw_numel(desc);
+  const size_t nw = n ? (size_t)desc->C_in * desc->K : 0;
+  if ((s = check_ptr(x, n, es, "x")) || (s = check_ptr(y, n, es, "y")) ||
+      (s = check_ptr(wcol, nw, 4, "wcol")) || (s = check_ptr(wrow, nw, 4, "wrow")))
+    return s;
+  if (overlap(x, y, n * es)) return fail(GIGA_ERR_INVALID_ARG, "y aliases x");
+  if (n == 0) return GIGA_OK;
+  DwArgs a = make_args(desc);
+  a.x = x;
+  a.y = y;
+  a.vec = vec_ok(a, x, y, nullptr);
+  cudaError_t e = dispatch_k(a.K, [&](auto k) {
+    return dw_sep_launch<decltype(k)::value>(a, wcol, wrow, static_cast<cudaStream_t>(stream));
+  });
+  return e == cudaSuccess ? GIGA_OK : cuda_fail(e, "separable launch");
+}
+
 // Shared checks of the two upsampling entry points; fills a.
 static giga_status_t up_prepare(const giga_conv2d_desc_t* desc, int32_t scale, const void* x,
                                 const void* y, UpArgs& a) {

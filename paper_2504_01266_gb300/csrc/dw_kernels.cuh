@@ -718,6 +718,133 @@ __global__ void __launch_bounds__(kThreads) dw_fwd_kernel(
     mbar_wait(bars + (sb ^ 1), (phase >> (sb ^ 1)) & 1u);
 }
 
+// ------------------------------------------------------ separable filter
+// y[c][i][j] = sum_a wcol[c][a] * t[i + a - r][j],
+// t[i][j]    = sum_b wrow[c][b] * x~[i][j + b - r]   (x~: the border applied),
+// the K x K filter wcol (x) wrow applied as a row pass then a column pass:
+// 2K instead of K^2 multiply-adds per pixel.  One 64 x 128 tile per CTA; the
+// halo tile is staged like the forward's (TMA or cp.async, clamp fix, BF16
+// widened); the row pass writes t over the first 128 columns of the same
+// staged row (a warp owns whole rows and reads a row completely before it
+// writes it), then the column pass runs down t in 8-row register blocks.
+template <int K, typename T>
+struct SepShape {
+  using G = Geo<K>;
+  static constexpr int TH = 64;
+  static constexpr int ROWS = TH + 2 * G::R;
+  using ST = HaloTile<K, T, ROWS>;
+  static constexpr int HEAD = 128;  // mbarrier, abort flag
+  static constexpr int W_OFF = HEAD + ST::BYTES;  // wrow then wcol, K floats each (padded)
+  static constexpr int SM_BYTES = W_OFF + 2 * round_up(K, 4) * 4;
+};
+
+template <typename T, int K>
+__global__ void __launch_bounds__(kThreads) dw_sep_kernel(
+    const __grid_constant__ CUtensorMap tmx, const T* __restrict__ x,
+    const float* __restrict__ wcol, const float* __restrict__ wrow, T* __restrict__ y, int C,
+    int H, int W, int tiles_x, int tiles_y, int clamp, int vec, int use_tma, int* err) {
+  using G = Geo<K>;
+  using GS = Geo<K, sizeof(T)>;
+  using S = SepShape<K, T>;
+  using ST = typename S::ST;
+  constexpr int KP = round_up(K, 4);
+  extern __shared__ __align__(128) float smem[];
+  char* sm = reinterpret_cast<char*>(smem);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sm);
+  float* st = reinterpret_cast<float*>(sm + S::HEAD);
+  float* swr = reinterpret_cast<float*>(sm + S::W_OFF);
+  float* swc = swr + KP;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t t = blockIdx.x;
+  const int tx0 = (int)(t % tiles_x) * kTileW;
+  const int64_t t2 = t / tiles_x;
+  const int ty0 = (int)(t2 % tiles_y) * S::TH;
+  const int64_t plane = t2 / tiles_y;
+  const int c = (int)(plane % C);
+
+  for (int k = threadIdx.x; k < 2 * KP; k += kThreads) {
+    const int b = k < KP ? k : k - KP;
+    const float* src = (k < KP ? wrow : wcol) + (int64_t)c * K;
+    cp_async4(swr + k, b < K ? src + b : src, b < K);
+  }
+  volatile int* s_abort = reinterpret_cast<volatile int*>(sm + 8);
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    *s_abort = 0;
+    mbar_init_fence();
+  }
+  cta_barrier();
+  T* staged = reinterpret_cast<T*>(sm + S::HEAD + ST::STAGE_OFF);
+  if (use_tma) {
+    cp_async_commit();
+    if (threadIdx.x == 0) {
+      fence_proxy_async();
+      mbar_expect_tx(bar, (uint32_t)ST::STAGE_BYTES);
+      tma_load_3d(staged, &tmx, tx0 - GS::RP, ty0 - G::R, (int)plane, bar);
+    }
+    cp_async_wait_all();
+    if (!mbar_wait(bar, 0)) {
+      record_error(err, kDevErrTimeout);
+      *s_abort = 1;
+    }
+  } else {
+    stage_tile<T, G::R, GS::RP, GS::SP>(staged, x + plane * (int64_t)H * W, H, W, ty0, tx0,
+                                        S::ROWS, clamp != 0, vec != 0);
+    cp_async_wait_all();
+  }
+  cta_barrier();
+  if (*s_abort) {
+    mbar_wait(bar, 0);  // let a late copy land (bounded) before the CTA exits
+    return;
+  }
+  if constexpr (sizeof(T) == 2)
+    widen_halo_tile<K, S::ROWS, kThreads>(st, reinterpret_cast<const __nv_bfloat16*>(staged));
+  if (use_tma && clamp &&
+      (ty0 - G::R < 0 || ty0 + S::TH + G::R > H || tx0 - G::RP < 0 || tx0 + kTileW + G::RP > W))
+    clamp_fix<float, G::SP, kThreads>(st, H, W, ty0, tx0, G::R, G::RP, S::ROWS);
+
+  // row pass, in place: row sr of t = columns [0, 128) of staged row sr
+  for (int sr = warp; sr < S::ROWS; sr += kWarps) {
+    float buf[4 * G::NV];
+    load_window_row<K, float>(st + sr * G::SP + 4 * lane, buf);
+    float o[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int b = 0; b < K; ++b) {
+      const float wb = swr[b];
+#pragma unroll
+      for (int px = 0; px < 4; ++px) o[px] = fmaf(wb, buf[G::OFFR + px + b], o[px]);
+    }
+    __syncwarp();  // every lane has read the row before any lane overwrites it
+    *reinterpret_cast<float4*>(st + sr * G::SP + 4 * lane) = make_float4(o[0], o[1], o[2], o[3]);
+  }
+  cta_barrier();
+
+  // column pass: warp w owns output rows 8w .. 8w + 7
+  constexpr int PY = 8;
+  float acc[PY][4];
+#pragma unroll
+  for (int py = 0; py < PY; ++py)
+#pragma unroll
+    for (int px = 0; px < 4; ++px) acc[py][px] = 0.f;
+#pragma unroll
+  for (int ir = 0; ir < PY + K - 1; ++ir) {
+    const float4 v = *reinterpret_cast<const float4*>(st + (warp * PY + ir) * G::SP + 4 * lane);
+#pragma unroll
+    for (int a = 0; a < K; ++a) {
+      const int py = ir - a;
+      if (py >= 0 && py < PY) {
+        const float wa = swc[a];
+        acc[py][0] = fmaf(wa, v.x, acc[py][0]);
+        acc[py][1] = fmaf(wa, v.y, acc[py][1]);
+        acc[py][2] = fmaf(wa, v.z, acc[py][2]);
+        acc[py][3] = fmaf(wa, v.w, acc[py][3]);
+      }
+    }
+  }
+  store_block<T, PY>(y + plane * (int64_t)H * W, H, W, ty0 + warp * PY, tx0 + 4 * lane,
+                     vec != 0, acc);
+}
+
 // -------------------------------------------------------------- backward
 // Fused backward: warps 0-3 write g (= dx for the zero border) from the staged
 // dy tile, warps 4-7 accumulate dw from the staged x and dy tiles.  A CTA owns

@@ -18,6 +18,12 @@ template <int K>
 cudaError_t dw_fwd_launch(const DwArgs& a, const DwConfig& cfg, bool input_grad,
                           cudaStream_t st);
 
+// Separable filter wcol (x) wrow [C][K] each: a row pass then a column pass
+// in one launch (y = the forward with the outer-product filter, border of a).
+template <int K>
+cudaError_t dw_sep_launch(const DwArgs& a, const float* wcol, const float* wrow,
+                          cudaStream_t st);
+
 // Fused backward tile pass: g (the input gradient before the clamp edge
 // fold) and the filter partials[planes * chunks][K*K].
 template <int K>
@@ -59,6 +65,8 @@ cudaError_t dw_finalize_launch(const DwArgs& a, int64_t chunks_per_plane, cudaSt
 
 #define GIGA_DW_EXTERN(K)                                                                  \
   extern template cudaError_t dw_fwd_launch<K>(const DwArgs&, const DwConfig&, bool,      \
+                                               cudaStream_t);                              \
+  extern template cudaError_t dw_sep_launch<K>(const DwArgs&, const float*, const float*, \
                                                cudaStream_t);
 #define GIGA_DW_EXTERN_BWD(K)                                                              \
   extern template cudaError_t dw_bwd_launch<K>(const DwArgs&, const DwConfig&,            \

@@ -162,8 +162,39 @@ cudaError_t dw_filter_launch(const DwArgs& a, const DwConfig& cfg, cudaStream_t 
   }
 }
 
+template <typename T, int K>
+static cudaError_t sep_impl(const DwArgs& a, const float* wcol, const float* wrow,
+                            cudaStream_t st) {
+  using S = SepShape<K, T>;
+  cudaError_t e = set_smem_once<dw_sep_kernel<T, K>>((size_t)S::SM_BYTES);
+  if (e != cudaSuccess) return e;
+  const int64_t tiles_x = (a.W + kTileW - 1) / kTileW;
+  const int64_t tiles_y = (a.H + S::TH - 1) / S::TH;
+  const int64_t grid = a.N * a.C * tiles_x * tiles_y;
+  if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  CUtensorMap tm;
+  std::memset(&tm, 0, sizeof(tm));
+  int use_tma = 0;
+  if (plane_tma_ok(a.x, sizeof(T), a.W))
+    use_tma = make_plane_map(&tm, a.x, sizeof(T), a.W, a.H, a.N * a.C, Geo<K, sizeof(T)>::SP,
+                             S::ROWS);
+  dw_sep_kernel<T, K><<<(unsigned)grid, kThreads, (size_t)S::SM_BYTES, st>>>(
+      tm, static_cast<const T*>(a.x), wcol, wrow, static_cast<T*>(a.y), (int)a.C, (int)a.H,
+      (int)a.W, (int)tiles_x, (int)tiles_y, a.border, a.vec, use_tma, dw_error_word());
+  note_launch();
+  return cudaGetLastError();
+}
+
+template <int K>
+cudaError_t dw_sep_launch(const DwArgs& a, const float* wcol, const float* wrow,
+                          cudaStream_t st) {
+  return a.dtype == 0 ? sep_impl<float, K>(a, wcol, wrow, st)
+                      : sep_impl<__nv_bfloat16, K>(a, wcol, wrow, st);
+}
+
 #define GIGA_DW_INSTANTIATE(K)                                                            \
-  template cudaError_t dw_fwd_launch<K>(const DwArgs&, const DwConfig&, bool, cudaStream_t);
+  template cudaError_t dw_fwd_launch<K>(const DwArgs&, const DwConfig&, bool, cudaStream_t); \
+  template cudaError_t dw_sep_launch<K>(const DwArgs&, const float*, const float*, cudaStream_t);
 #define GIGA_DW_INSTANTIATE_BWD(K)                                                        \
   template cudaError_t dw_bwd_launch<K>(const DwArgs&, const DwConfig&, cudaStream_t);      \
   template cudaError_t dw_filter_launch<K>(const DwArgs&, const DwConfig&, cudaStream_t);
