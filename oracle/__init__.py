@@ -82,6 +82,7 @@ def _load():
             "oracle_dense_bwd_filter_taps": [_D, _D] + dense + [_I64P, _I64, _D],
             "oracle_upsample_nearest": [_D, _D, _I64, _I64, _I64, _I64],
             "oracle_upsample_dw_fwd_points": [_D, _D] + six + [_I64, _I64P, _I64, _D],
+            "oracle_rgb_to_gray": [_D, _D, _I64, _I64, _I64],
         }
         for name, args in sigs.items():
             fn = getattr(lib, name)
@@ -294,6 +295,7 @@ class use_library:
                      "oracle_dense_bwd_input", "oracle_dense_bwd_input_points",
                      "oracle_dense_bwd_filter", "oracle_dense_bwd_filter_taps",
                      "oracle_upsample_nearest", "oracle_upsample_dw_fwd_points",
+                     "oracle_rgb_to_gray",
                      "oracle_num_threads"):
             src, dst = getattr(self.saved, name), getattr(lib, name)
             dst.argtypes, dst.restype = src.argtypes, src.restype
@@ -349,3 +351,22 @@ def dw_fwd_separable(x, wcol, wrow, border: int) -> np.ndarray:
     if wc.ndim != 2 or wc.shape != wr.shape:
         raise ValueError("wcol and wrow must both be (C, K)")
     return dw_fwd(x, wc[:, :, None] * wr[:, None, :], border)
+
+
+# ------------------------------------------------------------------ grayscale
+
+def rgb_to_gray(x) -> np.ndarray:
+    """Section 4.2.5: gray = 0.299 R + 0.587 G + 0.114 B; x (N, 3, H, W) ->
+    (N, 1, H, W)."""
+    x = _f64(x)
+    if x.ndim != 4 or x.shape[1] != 3:
+        raise ValueError("x must be (N, 3, H, W)")
+    N, _, H, W = x.shape
+    g = np.empty((N, 1, H, W), dtype=np.float64)
+    _check(_load().oracle_rgb_to_gray(_p(x), _p(g), N, H, W), "rgb_to_gray")
+    return g
+
+
+def gray_dw_fwd(x, w, border: int) -> np.ndarray:
+    """Grayscale conversion, then the filter w (1, K, K) on the gray image."""
+    return dw_fwd(rgb_to_gray(x), w, border)

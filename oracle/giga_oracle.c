@@ -23,7 +23,9 @@
  *     channel), which is the same neighbourhood sum with one more index;
  *   - nearest-neighbour upsampling by an integer factor (Section 4.2.3), and
  *     the paper's sharpening benchmark (Section 6.6): the filter applied to
- *     the upsampled image.
+ *     the upsampled image;
+ *   - RGB to grayscale conversion (Section 4.2.5), the luminance weights
+ *     0.299, 0.587, 0.114 of the red, green and blue channels.
  *
  * Conventions (plain definitions, no blocking or reordering):
  *   r = (K - 1) / 2, tap (a, b) with a, b in [0, K) reads the neighbour at
@@ -436,5 +438,21 @@ int oracle_upsample_dw_fwd_points(const double* x, const double* w, int64_t N, i
         }
         out[k] = sum;
     }
+    return 0;
+}
+
+/* ------------------------------------------------------------- grayscale */
+
+/* RGB to grayscale (Section 4.2.5): gray = 0.299 R + 0.587 G + 0.114 B per
+ * pixel; x is N x 3 x H x W (channels R, G, B), gray is N x 1 x H x W. */
+int oracle_rgb_to_gray(const double* x, double* gray, int64_t N, int64_t H, int64_t W) {
+    if (N < 0 || H < 0 || W < 0) return 1;
+    const int64_t P = H * W;
+#pragma omp parallel for schedule(static)
+    for (int64_t n = 0; n < N; ++n)
+        for (int64_t p = 0; p < P; ++p) {
+            const double* px = x + n * 3 * P + p;
+            gray[n * P + p] = 0.299 * px[0] + 0.587 * px[P] + 0.114 * px[2 * P];
+        }
     return 0;
 }

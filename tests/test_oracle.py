@@ -388,10 +388,36 @@ def pin_separable_filter():
         assert rel(oracle.dw_fwd_separable(x, wr, wc, ZERO), t.numpy()) > 1e-3, K
 
 
+def pin_grayscale():
+    """Section 4.2.5's luminance weights: pure red, green and blue images give
+    0.299, 0.587 and 0.114 times their value; equal channels give the value
+    back (the weights sum to 1); the conversion equals the weighted channel sum
+    computed by numpy and by torch, and composes with the filter."""
+    g = rng(24)
+    x = g.standard_normal((2, 3, 5, 7))
+    want = 0.299 * x[:, 0] + 0.587 * x[:, 1] + 0.114 * x[:, 2]
+    got = oracle.rgb_to_gray(x)
+    assert got.shape == (2, 1, 5, 7)
+    assert rel(got[:, 0], want) < 1e-15
+    t = (torch.from_numpy(x) * torch.tensor([0.299, 0.587, 0.114], dtype=torch.float64)[:, None, None]).sum(1)
+    assert rel(got[:, 0], t.numpy()) < 1e-15
+    for ch, coef in enumerate((0.299, 0.587, 0.114)):
+        pure = np.zeros((1, 3, 2, 2))
+        pure[0, ch] = 2.0
+        assert np.allclose(oracle.rgb_to_gray(pure), 2.0 * coef, rtol=1e-15, atol=0)
+    same = np.repeat(x[:, :1], 3, axis=1)
+    assert rel(oracle.rgb_to_gray(same), x[:, :1]) < 1e-15
+    w = g.standard_normal((1, 3, 3))
+    for border in (ZERO, CLAMP):
+        assert rel(oracle.gray_dw_fwd(x, w, border),
+                   oracle.dw_fwd(want[:, None], w, border)) < 1e-14
+
+
 PINS = [pin_golden, pin_delta, pin_shift, pin_box_constant, pin_torch_crosscheck,
         pin_separable_gaussian, pin_linearity, pin_translation, pin_operator_bruteforce,
         pin_adjoint, pin_filter_bilinear, pin_finite_differences, pin_points_match_full,
-        pin_dense, pin_upsample_nearest, pin_upsample_sharpen, pin_separable_filter]
+        pin_dense, pin_upsample_nearest, pin_upsample_sharpen, pin_separable_filter,
+        pin_grayscale]
 
 
 @pytest.mark.parametrize("pin", PINS, ids=[p.__name__ for p in PINS])
@@ -446,6 +472,9 @@ MUTATIONS = {
     "upsample_points_border_on_input": (
         "sum += f[a * K + b] * plane[(su / s) * W + sv / s];",
         "sum += f[a * K + b] * plane[(i / s + a - r < 0 ? 0 : su / s) * W + sv / s];"),
+    "gray_weights_swapped": (
+        "gray[n * P + p] = 0.299 * px[0] + 0.587 * px[P] + 0.114 * px[2 * P];",
+        "gray[n * P + p] = 0.114 * px[0] + 0.587 * px[P] + 0.299 * px[2 * P];"),
     "dense_grad_sign": (
         "sum += dy[((n * H + i) * W + j) * Co + o] * x[((n * H + si) * W + sj) * Ci + c];",
         "sum -= dy[((n * H + i) * W + j) * Co + o] * x[((n * H + si) * W + sj) * Ci + c];"),
