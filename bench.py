@@ -503,6 +503,60 @@ def compare_separable(dev, iters):
     return out
 
 
+def compare_gray(dev, iters):
+    """Grayscale then filter (Sections 4.2.5, 4.2.4) on 8 RGB images of
+    4096 x 4096 FP32 with the paper's 3 x 3 Laplacian, zero border: the fused
+    pass (gray formed in shared memory) vs the two calls (convert, then
+    filter), with the fused pass's HBM fraction (12 bytes read + 4 written per
+    gray pixel) and sampled errors against the oracle."""
+    import torch
+    import oracle
+    import workloads
+    from paper_2504_01266_gb300 import _lib as L
+    pk = peaks()
+    x, _ = workloads.plain_scale(3)          # 8 x 3 x 4096 x 4096, read as R, G, B
+    xd = x.to(dev)
+    Nn, _, Hh, Ww = x.shape
+    lap = torch.tensor([[[-1.0, -1, -1], [-1, 8, -1], [-1, -1, -1]]], device=dev)
+    y = torch.empty((Nn, 1, Hh, Ww), device=dev)
+    g = torch.empty_like(y)
+    stream = torch.cuda.current_stream(dev)
+    sp = stream.cuda_stream
+    d = L.desc(Nn, 3, 1, Hh, Ww, 3, 1, 0, L.GIGA_F32, L.GIGA_LAYOUT_NCHW)
+    dg = L.desc(Nn, 1, 1, Hh, Ww, 3, 1, 0, L.GIGA_F32, L.GIGA_LAYOUT_NCHW)
+
+    def fused():
+        L.check(L.giga_gray_conv2d_fwd(d, xd.data_ptr(), lap.data_ptr(), y.data_ptr(), sp), "gray")
+
+    def two():
+        L.check(L.giga_rgb_to_gray(d, xd.data_ptr(), g.data_ptr(), sp), "rgb_to_gray")
+        L.check(L.giga_conv2d_fwd(dg, g.data_ptr(), lap.data_ptr(), y.data_ptr(), None, 0, sp),
+                "fwd")
+    t_two = _events(stream, two, iters)
+    t_fused = _events(stream, fused, iters)
+    fused()
+    idx = workloads.sample_indices(y.numel(), 1500, salt=81)
+    got = y.reshape(-1)[idx.to(dev)].double().cpu().numpy()
+    flat = idx.numpy()
+    n_img, rest = flat // (Hh * Ww), flat % (Hh * Ww)
+    ref = []
+    for n in sorted(set(n_img.tolist())):
+        sel = n_img == n
+        gray = oracle.rgb_to_gray(x[n:n + 1].numpy())
+        ref.append((sel, oracle.dw_fwd_points(gray, lap.cpu().numpy(), 0, rest[sel])))
+    refv = got.copy()
+    for sel, vals in ref:
+        refv[sel] = vals
+    gbs = 16 * Nn * Hh * Ww / (t_fused * 1e-3) / 1e9
+    del xd, y, g
+    torch.cuda.empty_cache()
+    return {"workload": "8 RGB images 3x4096x4096 FP32, paper's 3x3 Laplacian on the gray image, "
+                        "zero border",
+            "fused_ms": t_fused, "two_pass_ms": t_two, "speedup": t_two / t_fused,
+            "fused_gbs": gbs, "fused_frac_of_hbm": gbs / pk["hbm_gbs"],
+            "err_normwise_sampled": _normwise(got, refv)}
+
+
 def compare_dense(dev, iters, bf16_peak):
     """Dense 3 x 3, 64 -> 64 channels, 8 x 1024 x 1024 BF16 NHWC on tcgen05:
     forward, input gradient and filter gradient, TFLOP/s against the measured
@@ -778,7 +832,8 @@ def run_giga(args):
                          ("ragged", lambda: compare_ragged(dev, 5)),
                          ("dense", lambda: compare_dense(dev, 10, bf16_peak)),
                          ("upsample_sharpen", lambda: compare_upsample(dev, 10)),
-                         ("separable", lambda: compare_separable(dev, 10))):
+                         ("separable", lambda: compare_separable(dev, 10)),
+                         ("gray_sharpen", lambda: compare_gray(dev, 10))):
             compare[name] = fn()
             torch.cuda.empty_cache()
 
@@ -829,7 +884,8 @@ def run_section(args):
           "ragged": lambda: compare_ragged(dev, args.steps),
           "dense": lambda: compare_dense(dev, args.steps, peak),
           "upsample": lambda: compare_upsample(dev, args.steps),
-          "separable": lambda: compare_separable(dev, args.steps)}[args.section]
+          "separable": lambda: compare_separable(dev, args.steps),
+          "gray": lambda: compare_gray(dev, args.steps)}[args.section]
     print(json.dumps({"section": args.section, "result": fn()}))
     return 0
 
@@ -851,7 +907,8 @@ def main():
                          "else tune and save the choices there")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the BF16 / ragged / dense comparison measurements")
-    ap.add_argument("--section", choices=["bf16", "ragged", "dense", "upsample", "separable"],
+    ap.add_argument("--section",
+                    choices=["bf16", "ragged", "dense", "upsample", "separable", "gray"],
                     help="run only this comparison and print its result (profiling aid)")
     ap.add_argument("--images", type=int, default=N,
                     help="images per GPU (profiling runs use 1: 201 MB per tensor, above L2)")

@@ -208,6 +208,22 @@ giga_status_t giga_upsample_conv2d_fwd(const giga_conv2d_desc_t* desc, int32_t s
                                        const void* x, const void* w, void* y, void* stream);
 
 /* ------------------------------------------------------------------------
+ * Grayscale (Section 4.2.5): gray = 0.299 R + 0.587 G + 0.114 B per pixel.
+ * desc: N images, C_in = 3 (channels R, G, B), C_out = 1, groups = 1, NCHW,
+ * FP32 or BF16; x is N x 3 x H x W, y is N x 1 x H x W in the same type, not
+ * aliasing x.
+ * giga_rgb_to_gray: the conversion alone (desc->K, desc->border checked,
+ *   not used).
+ * giga_gray_conv2d_fwd: the K x K filter w[1][K][K] (FP32, odd K <= 15)
+ *   applied to the gray image with desc->border, in one pass: the gray
+ *   image is formed in shared memory and never stored.
+ * Asynchronous on `stream`. */
+giga_status_t giga_rgb_to_gray(const giga_conv2d_desc_t* desc, const void* x, void* y,
+                               void* stream);
+giga_status_t giga_gray_conv2d_fwd(const giga_conv2d_desc_t* desc, const void* x, const float* w,
+                                   void* y, void* stream);
+
+/* ------------------------------------------------------------------------
  * Autotuner.  Candidates: forward and input gradient (op 1 / 2): id 0..3 =
  * {8, 4} rows per thread (bit 0) x {one tile per CTA, persistent
  * double-buffered CTAs} (bit 1); filter gradient (op 4): id 0..4 = tiles

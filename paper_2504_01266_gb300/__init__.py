@@ -23,7 +23,7 @@ DTYPES = {torch.float32: _lib.GIGA_F32, torch.bfloat16: _lib.GIGA_BF16}
 
 __all__ = ["conv2d", "conv2d_fwd", "conv2d_bwd", "conv2d_bwd_input", "conv2d_bwd_filter",
            "DepthwiseConv2d", "workspace", "BORDERS", "upsample_nearest", "upsample_conv2d",
-           "conv2d_separable"]
+           "conv2d_separable", "rgb_to_gray", "gray_conv2d"]
 
 
 def _border(border) -> int:
@@ -92,6 +92,34 @@ def conv2d_separable(x: torch.Tensor, wcol: torch.Tensor, wrow: torch.Tensor, bo
     y = torch.empty_like(x) if out is None else out
     _lib.check(_lib.giga_conv2d_fwd_separable(d, _ptr(x), _ptr(wcol), _ptr(wrow), _ptr(y),
                                               _stream(x.device)), "giga_conv2d_fwd_separable")
+    return y
+
+
+def _gray_desc(x: torch.Tensor, K: int, border):
+    if x.dim() != 4 or x.shape[1] != 3:
+        raise ValueError("x must be (N, 3, H, W) with channels R, G, B")
+    N, _, H, W = x.shape
+    return _lib.desc(N, 3, 1, H, W, K, 1, _border(border), _dtype(x), _lib.GIGA_LAYOUT_NCHW)
+
+
+def rgb_to_gray(x: torch.Tensor, out=None) -> torch.Tensor:
+    """gray = 0.299 R + 0.587 G + 0.114 B: (N, 3, H, W) -> (N, 1, H, W)."""
+    _require_cuda(x)
+    d = _gray_desc(x, 1, "zero")
+    y = torch.empty((x.shape[0], 1) + tuple(x.shape[2:]), dtype=x.dtype, device=x.device) \
+        if out is None else out
+    _lib.check(_lib.giga_rgb_to_gray(d, _ptr(x), _ptr(y), _stream(x.device)), "giga_rgb_to_gray")
+    return y
+
+
+def gray_conv2d(x: torch.Tensor, w: torch.Tensor, border="zero", out=None) -> torch.Tensor:
+    """The filter w (1, K, K) applied to the grayscale image of x, in one pass."""
+    _require_cuda(x, w)
+    d = _gray_desc(x, w.shape[-1], border)
+    y = torch.empty((x.shape[0], 1) + tuple(x.shape[2:]), dtype=x.dtype, device=x.device) \
+        if out is None else out
+    _lib.check(_lib.giga_gray_conv2d_fwd(d, _ptr(x), _ptr(w), _ptr(y), _stream(x.device)),
+               "giga_gray_conv2d_fwd")
     return y
 
 

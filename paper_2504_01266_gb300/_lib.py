@@ -38,6 +38,7 @@ EXPORTS = (
     "giga_conv2d_workspace_size", "giga_conv2d_fwd", "giga_conv2d_bwd_input",
     "giga_conv2d_bwd_filter", "giga_conv2d_bwd", "giga_conv2d_bwd_filter_noalloc",
     "giga_conv2d_fwd_separable", "giga_upsample_nearest", "giga_upsample_conv2d_fwd",
+    "giga_rgb_to_gray", "giga_gray_conv2d_fwd",
     "giga_batched_plan_create",
     "giga_batched_plan_workspace_size", "giga_batched_plan_upload", "giga_batched_plan_run",
     "giga_batched_plan_destroy", "giga_conv2d_batched", "giga_conv2d_batched_workspace_size",
@@ -91,6 +92,8 @@ _SIGS = {
     "giga_conv2d_bwd_filter_noalloc": (_ST, [_DESC, _P, _P, _P, _P]),
     "giga_conv2d_fwd_separable": (_ST, [_DESC, _P, _P, _P, _P, _P]),
     "giga_upsample_nearest": (_ST, [_DESC, _I32, _P, _P, _P]),
+    "giga_rgb_to_gray": (_ST, [_DESC, _P, _P, _P]),
+    "giga_gray_conv2d_fwd": (_ST, [_DESC, _P, _P, _P, _P]),
     "giga_upsample_conv2d_fwd": (_ST, [_DESC, _I32, _P, _P, _P, _P]),
     "giga_batched_plan_create": (_ST, [_IMG, _I32, _I32, _I32, _I32, ctypes.POINTER(_P)]),
     "giga_batched_plan_workspace_size": (_ST, [_P, ctypes.POINTER(_SZ)]),
@@ -185,6 +188,14 @@ def giga_conv2d_bwd(d, x, dy, w, dx, dw, ws, ws_bytes, stream) -> int:
 
 def giga_conv2d_fwd_separable(d, x, wcol, wrow, y, stream) -> int:
     return load().giga_conv2d_fwd_separable(ctypes.byref(d), x, wcol, wrow, y, stream)
+
+
+def giga_rgb_to_gray(d, x, y, stream) -> int:
+    return load().giga_rgb_to_gray(ctypes.byref(d), x, y, stream)
+
+
+def giga_gray_conv2d_fwd(d, x, w, y, stream) -> int:
+    return load().giga_gray_conv2d_fwd(ctypes.byref(d), x, w, y, stream)
 
 
 def giga_upsample_nearest(d, scale, x, y, stream) -> int:

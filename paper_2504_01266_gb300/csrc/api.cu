@@ -334,6 +334,62 @@ giga_status_t giga_conv2d_fwd_separable(const giga_conv2d_desc_t* desc, const vo
   return e == cudaSuccess ? GIGA_OK : cuda_fail(e, "separable launch");
 }
 
+// Shared checks of the two grayscale entry points; fills a.
+static giga_status_t gray_prepare(const giga_conv2d_desc_t* desc, const void* x, const void* y,
+                                  GrayArgs& a) {
+  giga_status_t s = check_desc(desc);
+  if (s != GIGA_OK) return s;
+  if (desc->C_in != 3 || desc->C_out != 1 || desc->groups != 1)
+    return fail(GIGA_ERR_INVALID_ARG, "grayscale takes C_in = 3 (R, G, B), C_out = 1, groups = 1");
+  if (desc->layout != GIGA_LAYOUT_NCHW) return fail(GIGA_ERR_UNSUPPORTED, "grayscale takes NCHW");
+  const size_t es = elem_size(desc->dtype);
+  const size_t px = (size_t)(desc->N * desc->H * desc->W);
+  if ((s = check_ptr(x, 3 * px, es, "x")) || (s = check_ptr(y, px, es, "y"))) return s;
+  if (px && (reinterpret_cast<uintptr_t>(x) < reinterpret_cast<uintptr_t>(y) + px * es) &&
+      (reinterpret_cast<uintptr_t>(y) < reinterpret_cast<uintptr_t>(x) + 3 * px * es))
+    return fail(GIGA_ERR_INVALID_ARG, "y aliases x");
+  std::memset(&a, 0, sizeof(a));
+  a.x = x;
+  a.y = const_cast<void*>(y);
+  a.N = desc->N;
+  a.H = desc->H;
+  a.W = desc->W;
+  a.K = desc->K;
+  a.border = desc->border;
+  a.dtype = desc->dtype;
+  const uintptr_t align = desc->dtype == GIGA_F32 ? 16 : 8;
+  a.vec = (desc->W % 4 == 0 && reinterpret_cast<uintptr_t>(x) % align == 0 &&
+           reinterpret_cast<uintptr_t>(y) % align == 0) ? 1 : 0;
+  return GIGA_OK;
+}
+
+giga_status_t giga_rgb_to_gray(const giga_conv2d_desc_t* desc, const void* x, void* y,
+                               void* stream) {
+  clear_error();
+  GrayArgs a;
+  giga_status_t s = gray_prepare(desc, x, y, a);
+  if (s != GIGA_OK) return s;
+  if (a.N * a.H * a.W == 0) return GIGA_OK;
+  cudaError_t e = gray_launch(a, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? GIGA_OK : cuda_fail(e, "grayscale launch");
+}
+
+giga_status_t giga_gray_conv2d_fwd(const giga_conv2d_desc_t* desc, const void* x, const float* w,
+                                   void* y, void* stream) {
+  clear_error();
+  GrayArgs a;
+  giga_status_t s = gray_prepare(desc, x, y, a);
+  if (s != GIGA_OK) return s;
+  if (desc->K > kMaxKFilter)
+    return fail(GIGA_ERR_UNSUPPORTED, "grayscale-then-filter supports K <= 15");
+  const size_t px = (size_t)(a.N * a.H * a.W);
+  if ((s = check_ptr(w, px ? (size_t)desc->K * desc->K : 0, 4, "w"))) return s;
+  if (px == 0) return GIGA_OK;
+  a.w = w;
+  cudaError_t e = gray_fwd_launch(a, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? GIGA_OK : cuda_fail(e, "grayscale-then-filter launch");
+}
+
 // Shared checks of the two upsampling entry points; fills a.
 static giga_status_t up_prepare(const giga_conv2d_desc_t* desc, int32_t scale, const void* x,
                                 const void* y, UpArgs& a) {

@@ -46,6 +46,18 @@ struct UpArgs {
 cudaError_t up_nearest_launch(const UpArgs& a, cudaStream_t st);
 cudaError_t up_fwd_launch(const UpArgs& a, cudaStream_t st);
 
+// RGB to grayscale, alone or followed by the filter (gray.cu): x is
+// N x 3 x H x W, y is N x 1 x H x W, w is 1 x K x K.
+struct GrayArgs {
+  const void* x;
+  const float* w;
+  void* y;
+  int64_t N, H, W;
+  int K, border, dtype, vec;
+};
+cudaError_t gray_launch(const GrayArgs& a, cudaStream_t st);
+cudaError_t gray_fwd_launch(const GrayArgs& a, cudaStream_t st);
+
 // Device error word of the depthwise kernels (nonzero after a bounded wait
 // gave up) for the current device; nullptr if unavailable.
 int* dw_error_word();
