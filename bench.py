@@ -766,50 +766,58 @@ def run_giga(args):
         s_h2d = torch.cuda.Stream(dev)
         s_d2h = torch.cuda.Stream(dev)
         torch.cuda.synchronize(dev)
-        e_steps = max(1, min(args.steps, 3))
-        barrier(world)
-        s0 = torch.cuda.Event(enable_timing=True)
-        s1 = torch.cuda.Event(enable_timing=True)
-        s0.record(stream)
-        s_h2d.wait_stream(stream)
-        s_d2h.wait_stream(stream)
-        inputs_free = [torch.cuda.Event(), torch.cuda.Event()]
-        for e in inputs_free:
-            e.record(stream)
-        outs_free = {K: torch.cuda.Event() for K in KS}
-        for K in KS:
-            outs_free[K].record(stream)
-        for it in range(e_steps):
-            bx, bdy = dx_in[it % 2]
-            s_h2d.wait_event(inputs_free[it % 2])
-            with torch.cuda.stream(s_h2d):
-                bx.copy_(hx, non_blocking=True)
-                bdy.copy_(hdy, non_blocking=True)
-            loaded = torch.cuda.Event()
-            loaded.record(s_h2d)
-            stream.wait_event(loaded)
+        e_steps = max(1, min(args.steps, 5))
+
+        def e2e_pass(n_steps):
+            """n_steps pipelined steps; returns device milliseconds for them."""
+            s0 = torch.cuda.Event(enable_timing=True)
+            s1 = torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+            s_h2d.wait_stream(stream)
+            s_d2h.wait_stream(stream)
+            inputs_free = [torch.cuda.Event(), torch.cuda.Event()]
+            for e in inputs_free:
+                e.record(stream)
+            outs_free = {K: torch.cuda.Event() for K in KS}
             for K in KS:
-                yk, dxk = outs[K]
-                stream.wait_event(outs_free[K])
-                d = descs[K]
-                L.check(L.giga_conv2d_fwd(d, bx.data_ptr(), filt[K].data_ptr(), yk.data_ptr(),
-                                          None, 0, sp), "fwd")
-                L.check(L.giga_conv2d_bwd(d, bx.data_ptr(), bdy.data_ptr(), filt[K].data_ptr(),
-                                          dxk.data_ptr(), dws[K].data_ptr(), ws.data_ptr(),
-                                          ws_bytes, sp), "bwd")
-                done = torch.cuda.Event()
-                done.record(stream)
-                s_d2h.wait_event(done)
-                with torch.cuda.stream(s_d2h):
-                    hy[K].copy_(yk, non_blocking=True)
-                    hdx[K].copy_(dxk, non_blocking=True)
-                    hdw[K].copy_(dws[K], non_blocking=True)
-                outs_free[K].record(s_d2h)
-            inputs_free[it % 2].record(stream)
-        stream.wait_stream(s_d2h)
-        s1.record(stream)
-        torch.cuda.synchronize(dev)
-        rate, e_ms = aggregate(taps_per_step(), s0.elapsed_time(s1) / e_steps, world)
+                outs_free[K].record(stream)
+            for it in range(n_steps):
+                bx, bdy = dx_in[it % 2]
+                s_h2d.wait_event(inputs_free[it % 2])
+                with torch.cuda.stream(s_h2d):
+                    bx.copy_(hx, non_blocking=True)
+                    bdy.copy_(hdy, non_blocking=True)
+                loaded = torch.cuda.Event()
+                loaded.record(s_h2d)
+                stream.wait_event(loaded)
+                for K in KS:
+                    yk, dxk = outs[K]
+                    stream.wait_event(outs_free[K])
+                    d = descs[K]
+                    L.check(L.giga_conv2d_fwd(d, bx.data_ptr(), filt[K].data_ptr(),
+                                              yk.data_ptr(), None, 0, sp), "fwd")
+                    L.check(L.giga_conv2d_bwd(d, bx.data_ptr(), bdy.data_ptr(),
+                                              filt[K].data_ptr(), dxk.data_ptr(),
+                                              dws[K].data_ptr(), ws.data_ptr(), ws_bytes, sp),
+                            "bwd")
+                    done = torch.cuda.Event()
+                    done.record(stream)
+                    s_d2h.wait_event(done)
+                    with torch.cuda.stream(s_d2h):
+                        hy[K].copy_(yk, non_blocking=True)
+                        hdx[K].copy_(dxk, non_blocking=True)
+                        hdw[K].copy_(dws[K], non_blocking=True)
+                    outs_free[K].record(s_d2h)
+                inputs_free[it % 2].record(stream)
+            stream.wait_stream(s_d2h)
+            s1.record(stream)
+            torch.cuda.synchronize(dev)
+            return s0.elapsed_time(s1)
+
+        e2e_pass(1)  # untimed: first use of the freshly pinned host buffers
+        barrier(world)
+        e_total = e2e_pass(e_steps)
+        rate, e_ms = aggregate(taps_per_step(), e_total / e_steps, world)
         elem = 4
         e2e = {"value": rate / 1e9, "unit": UNIT, "ms_per_step": e_ms,
                "h2d_bytes_per_step": 2 * px * elem,
