@@ -38,6 +38,7 @@ METRIC = "Gpixel*tap/s fwd+bwd (depthwise KxK, K in {3,7,15})"
 UNIT = "Gpixel*tap/s"
 WORKLOAD = "plain_scale: 8x3x4096x4096 fp32, depthwise K in {3,7,15} normal(0,0.1), clamp border, fwd+bwd"
 SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0   # GB300: FP32 FMA units and max clock
+RAGGED_IMAGES = None   # all 256 images of the ragged workload; a prefix for profiling runs
 
 
 def peaks():
@@ -58,6 +59,11 @@ def set_images(n: int):
     global N, WORKLOAD
     N = n
     WORKLOAD = WORKLOAD.replace("8x3x4096x4096", f"{n}x3x4096x4096")
+
+
+def set_ragged_images(n: int):
+    global RAGGED_IMAGES
+    RAGGED_IMAGES = n
 
 
 def taps_per_step():
@@ -341,7 +347,7 @@ def compare_ragged(dev, iters):
     import workloads
     import paper_2504_01266_gb300 as giga
     from paper_2504_01266_gb300 import _lib as L
-    shapes = workloads.ragged_shapes()
+    shapes = workloads.ragged_shapes()[:RAGGED_IMAGES]
     imgs, taps = [], 0
     for idx, (h, w_, k) in enumerate(shapes):
         g = workloads.generator("ragged", salt=idx + 1, device=str(dev))
@@ -383,7 +389,8 @@ def compare_ragged(dev, iters):
                for a, b, im in zip(ref_y, ref_dy, imgs[:4]))
     plan.close()
     px = sum(3 * h * w_ for h, w_, _ in shapes)
-    return {"workload": "256 images 3 x U[64,4096]^2, K in {3,5,9,11}, zero border, fwd+bwd",
+    return {"workload": f"{len(shapes)} images 3 x U[64,4096]^2, K in {{3,5,9,11}}, zero border, "
+                        "fwd+bwd",
             "pixels": px, "graph_persistent": {"ms": ms_graph, "value": taps / (ms_graph * 1e-3) / 1e9},
             "per_image_loop": {"ms": ms_loop, "value": taps / (ms_loop * 1e-3) / 1e9,
                                "launches": 4 * len(imgs)},
@@ -452,6 +459,82 @@ def compare_upsample(dev, iters):
     return out
 
 
+def compare_up_batched(dev, iters):
+    """The sharpening benchmark over a database of images (Sections 5 and 6.6):
+    128 RGB FP32 images, sides uniform in [64, 1024], each upsampled by its own
+    scale (2-8) and filtered with its own K x K filters (K in {3, 5, 9, 11}),
+    zero border.  The batched path (one launch per filter size, 4 here) replayed
+    from a CUDA graph vs a loop of single-image fused calls (one launch per
+    image) on the same GPU, with the batched path's output bandwidth and FP32
+    FMA rate against their peaks and sampled errors against the oracle."""
+    import torch
+    import numpy as np
+    import oracle
+    import workloads
+    import paper_2504_01266_gb300 as giga
+    from paper_2504_01266_gb300 import _lib as L
+    pk = peaks()
+    shapes = workloads.up_ragged_shapes()[:RAGGED_IMAGES]
+    host, imgs = [], []
+    for i, (h, w_, s, k) in enumerate(shapes):
+        x, w = workloads.up_ragged_image(i, h, w_, k)
+        host.append((x, w, s))
+        imgs.append({"x": x.to(dev), "w": w.to(dev), "scale": s,
+                     "y": torch.empty((3, h * s, w_ * s), device=dev)})
+    stream = torch.cuda.current_stream(dev)
+    sp = stream.cuda_stream
+    plan = giga.UpsampleBatchedPlan(imgs, "zero")
+    plan.upload()
+    torch.cuda.synchronize(dev)
+    side = torch.cuda.Stream(dev)
+    side.wait_stream(stream)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(graph, stream=side):
+            plan.run()
+    torch.cuda.synchronize(dev)
+    ms_graph = _events(stream, graph.replay, iters)
+    graph.replay()
+    torch.cuda.synchronize(dev)
+    first = [im["y"].reshape(-1)[:4096].clone() for im in imgs[:8]]
+    descs = [L.desc(1, 3, 3, h, w_, k, 3, 0, L.GIGA_F32, L.GIGA_LAYOUT_NCHW)
+             for h, w_, s, k in shapes]
+
+    def loop():
+        for d, im in zip(descs, imgs):
+            L.check(L.giga_upsample_conv2d_fwd(d, im["scale"], im["x"].data_ptr(),
+                                               im["w"].data_ptr(), im["y"].data_ptr(), sp),
+                    "upsample_conv2d")
+    ms_loop = _events(stream, loop, max(2, iters // 2))
+    same = all(torch.equal(a, im["y"].reshape(-1)[:4096]) for a, im in zip(first, imgs[:8]))
+    plan.close()
+    # sampled outputs of every 8th image against the oracle
+    worst = 0.0
+    for i in range(0, len(shapes), 8):
+        x, w, s = host[i]
+        y = imgs[i]["y"]
+        idx = workloads.sample_indices(y.numel(), 300, salt=300 + i)
+        got = y.reshape(-1)[idx.to(dev)].double().cpu().numpy()
+        ref = oracle.upsample_dw_fwd_points(x.numpy()[None], w.numpy(), 0, s, idx.numpy())
+        worst = max(worst, _normwise(got, ref))
+    px = sum(3 * h * w_ * s * s for h, w_, s, _ in shapes)
+    fma = sum(3 * h * w_ * s * s * k * k for h, w_, s, k in shapes)
+    nbytes = sum(4 * 3 * h * w_ * (s * s + 1) for h, w_, s, _ in shapes)   # write y, read x
+    gbs = nbytes / (ms_graph * 1e-3) / 1e9
+    tflops = 2 * fma / (ms_graph * 1e-3) / 1e12
+    del imgs, graph
+    torch.cuda.empty_cache()
+    return {"workload": f"{len(shapes)} RGB FP32 images, sides U[64,1024], per-image scale "
+                        "U{2..8} and KxK filters K in {3,5,9,11} normal(0,0.1), zero border",
+            "output_pixels": px, "gpixel_tap_s": fma / (ms_graph * 1e-3) / 1e9,
+            "graph_batched": {"ms": ms_graph, "launches": len({k for *_, k in shapes}),
+                              "gbs": gbs, "frac_of_hbm": gbs / pk["hbm_gbs"],
+                              "tflops": tflops, "frac_of_fp32": tflops / pk["fp32_tflops"]},
+            "per_image_loop": {"ms": ms_loop, "launches": len(shapes)},
+            "speedup": ms_loop / ms_graph, "equal_to_single_image_path": bool(same),
+            "err_normwise_sampled": worst}
+
+
 def compare_separable(dev, iters):
     """Separable filters (Gaussians, sigma = K / 6) on the benchmark images
     (8 x 3 x 4096 x 4096 FP32, clamp): the row-then-column path vs the general
@@ -463,13 +546,13 @@ def compare_separable(dev, iters):
     import workloads
     from paper_2504_01266_gb300 import _lib as L
     pk = peaks()
-    x, _ = workloads.plain_scale(3)
+    x, _ = workloads.plain_scale(3, N=N)
     xd = x.to(dev)
     y = torch.empty_like(xd)
     Nn, Cc, Hh, Ww = x.shape
     stream = torch.cuda.current_stream(dev)
     sp = stream.cuda_stream
-    out = {"workload": "8x3x4096x4096 FP32 U[0,1), Gaussian filters sigma = K/6 (row and "
+    out = {"workload": f"{N}x3x4096x4096 FP32 U[0,1), Gaussian filters sigma = K/6 (row and "
                        "column factors), clamp border", "K": {}}
     for K in (3, 7, 15):
         r = K // 2
@@ -514,7 +597,7 @@ def compare_gray(dev, iters):
     import workloads
     from paper_2504_01266_gb300 import _lib as L
     pk = peaks()
-    x, _ = workloads.plain_scale(3)          # 8 x 3 x 4096 x 4096, read as R, G, B
+    x, _ = workloads.plain_scale(3, N=N)     # N x 3 x 4096 x 4096, read as R, G, B
     xd = x.to(dev)
     Nn, _, Hh, Ww = x.shape
     lap = torch.tensor([[[-1.0, -1, -1], [-1, 8, -1], [-1, -1, -1]]], device=dev)
@@ -550,8 +633,8 @@ def compare_gray(dev, iters):
     gbs = 16 * Nn * Hh * Ww / (t_fused * 1e-3) / 1e9
     del xd, y, g
     torch.cuda.empty_cache()
-    return {"workload": "8 RGB images 3x4096x4096 FP32, paper's 3x3 Laplacian on the gray image, "
-                        "zero border",
+    return {"workload": f"{N} RGB images 3x4096x4096 FP32, paper's 3x3 Laplacian on the gray "
+                        "image, zero border",
             "fused_ms": t_fused, "two_pass_ms": t_two, "speedup": t_two / t_fused,
             "fused_gbs": gbs, "fused_frac_of_hbm": gbs / pk["hbm_gbs"],
             "err_normwise_sampled": _normwise(got, refv)}
@@ -840,6 +923,7 @@ def run_giga(args):
                          ("ragged", lambda: compare_ragged(dev, 5)),
                          ("dense", lambda: compare_dense(dev, 10, bf16_peak)),
                          ("upsample_sharpen", lambda: compare_upsample(dev, 10)),
+                         ("upsample_sharpen_batched", lambda: compare_up_batched(dev, 5)),
                          ("separable", lambda: compare_separable(dev, 10)),
                          ("gray_sharpen", lambda: compare_gray(dev, 10))):
             compare[name] = fn()
@@ -892,6 +976,7 @@ def run_section(args):
           "ragged": lambda: compare_ragged(dev, args.steps),
           "dense": lambda: compare_dense(dev, args.steps, peak),
           "upsample": lambda: compare_upsample(dev, args.steps),
+          "up_batched": lambda: compare_up_batched(dev, args.steps),
           "separable": lambda: compare_separable(dev, args.steps),
           "gray": lambda: compare_gray(dev, args.steps)}[args.section]
     print(json.dumps({"section": args.section, "result": fn()}))
@@ -916,13 +1001,19 @@ def main():
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the BF16 / ragged / dense comparison measurements")
     ap.add_argument("--section",
-                    choices=["bf16", "ragged", "dense", "upsample", "separable", "gray"],
+                    choices=["bf16", "ragged", "dense", "upsample", "up_batched", "separable",
+                             "gray"],
                     help="run only this comparison and print its result (profiling aid)")
+    ap.add_argument("--ragged-images", type=int, default=None,
+                    help="run the ragged comparisons on the first n of their images "
+                         "(profiling runs)")
     ap.add_argument("--images", type=int, default=N,
                     help="images per GPU (profiling runs use 1: 201 MB per tensor, above L2)")
     args = ap.parse_args()
     if args.images != N:
         set_images(args.images)
+    if args.ragged_images is not None:
+        set_ragged_images(args.ragged_images)
     if args.impl == "reference":
         return run_reference(args)
     if args.section:

@@ -208,6 +208,59 @@ giga_status_t giga_upsample_conv2d_fwd(const giga_conv2d_desc_t* desc, int32_t s
                                        const void* x, const void* w, void* y, void* stream);
 
 /* ------------------------------------------------------------------------
+ * The sharpening benchmark over a ragged "database" of images (the batch
+ * processing the paper gave up on, Section 5; the operation of Section 6.6
+ * per image): every image is upsampled by its own integer scale and filtered
+ * with its own depthwise filters.  All images of one filter size run in ONE
+ * launch (at most 8 launches per batch, however many images it holds), each
+ * CTA one output tile found through an image table in the workspace.
+ *
+ * One entry per image; device pointers, NCHW with N = 1:
+ *   x: [C][H][W] and y: [C][H * scale][W * scale] in the batch dtype (not
+ *   aliasing), w: [C][K][K] FP32.  Odd K <= 15 (GIGA_ERR_UNSUPPORTED above
+ *   15), scale >= 2 (scale 1 is the plain filter: giga_conv2d_batched with
+ *   GIGA_OP_FWD; GIGA_ERR_UNSUPPORTED), upsampled sides below 2^31.  Images
+ *   with no output pixels are skipped.  The border rule applies on each
+ *   upsampled image.  Every output equals giga_upsample_conv2d_fwd on that
+ *   image alone, bit for bit.  `reserved` must be 0. */
+typedef struct {
+    const void* x;
+    void* y;
+    const float* w;
+    int32_t H, W, C, K, scale;
+    int32_t reserved;
+} giga_up_image_t;
+
+typedef struct giga_upsample_batched_plan_s* giga_upsample_batched_plan_t;
+
+/* Build the image table on the host (images ordered by filter size, largest
+ * first, then by size).  The plan copies the descriptors; it owns host memory
+ * only.  The workspace (256-byte aligned) holds the table, which the kernels
+ * only read. */
+giga_status_t giga_upsample_batched_plan_create(const giga_up_image_t* images, int32_t n,
+                                                int32_t border, int32_t dtype,
+                                                giga_upsample_batched_plan_t* plan);
+giga_status_t giga_upsample_batched_plan_workspace_size(giga_upsample_batched_plan_t plan,
+                                                        size_t* bytes);
+/* Copy the table into the workspace (asynchronous on `stream`; the plan must
+ * outlive the copy -- giga_upsample_batched_plan_destroy waits for it). */
+giga_status_t giga_upsample_batched_plan_upload(giga_upsample_batched_plan_t plan, void* ws,
+                                                size_t ws_bytes, void* stream);
+/* One launch per filter size present in the batch.  Capturable into a CUDA
+ * graph once the table has been uploaded. */
+giga_status_t giga_upsample_batched_plan_run(giga_upsample_batched_plan_t plan, void* ws,
+                                             size_t ws_bytes, void* stream);
+void giga_upsample_batched_plan_destroy(giga_upsample_batched_plan_t plan);
+
+/* Convenience: create + upload + run + destroy (blocks until the table copy
+ * has left host memory; not capturable). */
+giga_status_t giga_upsample_conv2d_batched(const giga_up_image_t* images, int32_t n,
+                                           int32_t border, int32_t dtype, void* ws,
+                                           size_t ws_bytes, void* stream);
+giga_status_t giga_upsample_conv2d_batched_workspace_size(const giga_up_image_t* images,
+                                                          int32_t n, size_t* bytes);
+
+/* ------------------------------------------------------------------------
  * Grayscale (Section 4.2.5): gray = 0.299 R + 0.587 G + 0.114 B per pixel.
  * desc: N images, C_in = 3 (channels R, G, B), C_out = 1, groups = 1, NCHW,
  * FP32 or BF16; x is N x 3 x H x W, y is N x 1 x H x W in the same type, not

@@ -23,7 +23,8 @@ DTYPES = {torch.float32: _lib.GIGA_F32, torch.bfloat16: _lib.GIGA_BF16}
 
 __all__ = ["conv2d", "conv2d_fwd", "conv2d_bwd", "conv2d_bwd_input", "conv2d_bwd_filter",
            "DepthwiseConv2d", "workspace", "BORDERS", "upsample_nearest", "upsample_conv2d",
-           "conv2d_separable", "rgb_to_gray", "gray_conv2d"]
+           "conv2d_separable", "rgb_to_gray", "gray_conv2d", "BatchedPlan",
+           "UpsampleBatchedPlan"]
 
 
 def _border(border) -> int:
@@ -274,6 +275,57 @@ class BatchedPlan:
     def close(self):
         if self.plan:
             _lib.giga_batched_plan_destroy(self.plan)
+            self.plan = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class UpsampleBatchedPlan:
+    """Upsample-then-filter over a ragged list of images in one persistent launch
+    (giga_upsample_batched_plan_*).
+
+    ``images``: list of dicts with device tensors ``x`` (C, H, W), ``y``
+    (C, H * scale, W * scale) in the same dtype, ``w`` (C, K, K) FP32 and an
+    integer ``scale`` >= 2.  ``run()`` is capturable into a CUDA graph once
+    ``upload()`` has been issued.
+    """
+
+    def __init__(self, images, border="zero", dtype=torch.float32):
+        self.n = len(images)
+        arr = (_lib.giga_up_image_t * max(1, self.n))()
+        self.keep = []
+        dev = torch.device("cuda")
+        for i, im in enumerate(images):
+            C, H, W = im["x"].shape[-3:]
+            _require_cuda(im["x"], im["y"], im["w"])
+            arr[i] = _lib.giga_up_image_t(_ptr(im["x"]), _ptr(im["y"]), _ptr(im["w"]), H, W, C,
+                                          im["w"].shape[-1], int(im["scale"]), 0)
+            self.keep.append(im)
+            dev = im["x"].device
+        self.arr = arr
+        self.plan = _lib.giga_upsample_batched_plan_create(arr, self.n, _border(border),
+                                                           DTYPES[dtype])
+        self.ws_bytes = _lib.giga_upsample_batched_plan_workspace_size(self.plan)
+        self.ws = torch.empty(max(self.ws_bytes, 256), dtype=torch.uint8, device=dev)
+        self.device = dev
+
+    def upload(self):
+        _lib.check(_lib.giga_upsample_batched_plan_upload(self.plan, self.ws.data_ptr(),
+                                                          self.ws.numel(), _stream(self.device)),
+                   "giga_upsample_batched_plan_upload")
+
+    def run(self):
+        _lib.check(_lib.giga_upsample_batched_plan_run(self.plan, self.ws.data_ptr(),
+                                                       self.ws.numel(), _stream(self.device)),
+                   "giga_upsample_batched_plan_run")
+
+    def close(self):
+        if self.plan:
+            _lib.giga_upsample_batched_plan_destroy(self.plan)
             self.plan = None
 
     def __del__(self):

@@ -42,6 +42,10 @@ EXPORTS = (
     "giga_batched_plan_create",
     "giga_batched_plan_workspace_size", "giga_batched_plan_upload", "giga_batched_plan_run",
     "giga_batched_plan_destroy", "giga_conv2d_batched", "giga_conv2d_batched_workspace_size",
+    "giga_upsample_batched_plan_create", "giga_upsample_batched_plan_workspace_size",
+    "giga_upsample_batched_plan_upload", "giga_upsample_batched_plan_run",
+    "giga_upsample_batched_plan_destroy", "giga_upsample_conv2d_batched",
+    "giga_upsample_conv2d_batched_workspace_size",
     "giga_autotune_set_mode", "giga_autotune_get_mode", "giga_autotune_conv2d",
     "giga_autotune_choice", "giga_autotune_set_choice", "giga_autotune_save",
     "giga_autotune_load", "giga_autotune_clear",
@@ -67,6 +71,12 @@ class giga_image_t(ctypes.Structure):
                 ("K", ctypes.c_int32)]
 
 
+class giga_up_image_t(ctypes.Structure):
+    _fields_ = [("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("w", ctypes.c_void_p),
+                ("H", ctypes.c_int32), ("W", ctypes.c_int32), ("C", ctypes.c_int32),
+                ("K", ctypes.c_int32), ("scale", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
 class GigaError(RuntimeError):
     def __init__(self, status: int, where: str, detail: str):
         super().__init__(f"{where}: {status_string(status)} ({detail})")
@@ -79,6 +89,7 @@ _lib = None
 _P = ctypes.c_void_p
 _DESC = ctypes.POINTER(giga_conv2d_desc_t)
 _IMG = ctypes.POINTER(giga_image_t)
+_UPIMG = ctypes.POINTER(giga_up_image_t)
 _SZ = ctypes.c_size_t
 _I32 = ctypes.c_int32
 _ST = ctypes.c_int32
@@ -102,6 +113,13 @@ _SIGS = {
     "giga_batched_plan_destroy": (None, [_P]),
     "giga_conv2d_batched": (_ST, [_IMG, _I32, _I32, _I32, _I32, _P, _SZ, _P]),
     "giga_conv2d_batched_workspace_size": (_ST, [_IMG, _I32, _I32, ctypes.POINTER(_SZ)]),
+    "giga_upsample_batched_plan_create": (_ST, [_UPIMG, _I32, _I32, _I32, ctypes.POINTER(_P)]),
+    "giga_upsample_batched_plan_workspace_size": (_ST, [_P, ctypes.POINTER(_SZ)]),
+    "giga_upsample_batched_plan_upload": (_ST, [_P, _P, _SZ, _P]),
+    "giga_upsample_batched_plan_run": (_ST, [_P, _P, _SZ, _P]),
+    "giga_upsample_batched_plan_destroy": (None, [_P]),
+    "giga_upsample_conv2d_batched": (_ST, [_UPIMG, _I32, _I32, _I32, _P, _SZ, _P]),
+    "giga_upsample_conv2d_batched_workspace_size": (_ST, [_UPIMG, _I32, ctypes.POINTER(_SZ)]),
     "giga_autotune_set_mode": (_ST, [_I32]),
     "giga_autotune_get_mode": (_I32, []),
     "giga_autotune_conv2d": (_ST, [_DESC, _I32, _P, _P, _P, _P, _P, _P, _P, _SZ, _P]),
@@ -240,6 +258,43 @@ def giga_conv2d_batched_workspace_size(images, n, ops) -> int:
     size = _SZ(0)
     check(load().giga_conv2d_batched_workspace_size(images, n, ops, ctypes.byref(size)),
           "giga_conv2d_batched_workspace_size")
+    return int(size.value)
+
+
+def giga_upsample_batched_plan_create(images, n, border, dtype):
+    plan = _P(None)
+    check(load().giga_upsample_batched_plan_create(images, n, border, dtype, ctypes.byref(plan)),
+          "giga_upsample_batched_plan_create")
+    return plan
+
+
+def giga_upsample_batched_plan_workspace_size(plan) -> int:
+    n = _SZ(0)
+    check(load().giga_upsample_batched_plan_workspace_size(plan, ctypes.byref(n)),
+          "giga_upsample_batched_plan_workspace_size")
+    return int(n.value)
+
+
+def giga_upsample_batched_plan_upload(plan, ws, ws_bytes, stream) -> int:
+    return load().giga_upsample_batched_plan_upload(plan, ws, ws_bytes, stream)
+
+
+def giga_upsample_batched_plan_run(plan, ws, ws_bytes, stream) -> int:
+    return load().giga_upsample_batched_plan_run(plan, ws, ws_bytes, stream)
+
+
+def giga_upsample_batched_plan_destroy(plan) -> None:
+    load().giga_upsample_batched_plan_destroy(plan)
+
+
+def giga_upsample_conv2d_batched(images, n, border, dtype, ws, ws_bytes, stream) -> int:
+    return load().giga_upsample_conv2d_batched(images, n, border, dtype, ws, ws_bytes, stream)
+
+
+def giga_upsample_conv2d_batched_workspace_size(images, n) -> int:
+    size = _SZ(0)
+    check(load().giga_upsample_conv2d_batched_workspace_size(images, n, ctypes.byref(size)),
+          "giga_upsample_conv2d_batched_workspace_size")
     return int(size.value)
 
 

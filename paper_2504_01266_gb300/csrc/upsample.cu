@@ -13,30 +13,10 @@
 
 #include <algorithm>
 
-#include "dw_kernels.cuh"
 #include "dw_launch.h"
+#include "upsample.cuh"
 
 namespace giga {
-
-// Unsigned division by a fixed divisor d >= 1 as a multiply-high and a shift
-// (round-up reciprocal; exact for every n < 2^31).
-struct FastDiv {
-  uint32_t mul, shift, d;
-};
-
-static FastDiv make_fastdiv(uint32_t d) {
-  FastDiv f{0, 0, d};
-  if (d == 1) return f;
-  uint32_t l = 0;
-  while ((1u << l) < d) ++l;
-  f.shift = l - 1;
-  f.mul = (uint32_t)((((uint64_t)1 << (32 + f.shift)) + d - 1) / d);
-  return f;
-}
-
-__device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv& f) {
-  return f.d == 1 ? n : (__umulhi(n, f.mul) >> f.shift);
-}
 
 // --------------------------------------------------------------- upsample
 // One thread per 4 consecutive outputs of a row (a 16/8-byte store when the
@@ -76,28 +56,6 @@ __global__ void __launch_bounds__(256) up_nearest_kernel(const T* __restrict__ x
 }
 
 // ------------------------------------------------- upsample, then filter
-// One 64 x 128 output tile of the upsampled grid per CTA (8 warps, 8 rows
-// each), scale s >= 2 (scale 1 is the plain forward).  The input pixels the
-// halo tile needs -- rows and columns of the upsampled window divided by s,
-// clamped to the image -- are first copied to shared memory; then every
-// shared cell (sr, sc) of the FP32 halo tile, upsampled pixel
-// (u, v) = (ty0 - r + sr, tx0 - RP + sc), takes the border rule on the
-// upsampled image (zero: the cell is 0; clamp: (u, v) clamped) and reads the
-// copied input pixel (u / s, v / s).  The forward loop and the store are the
-// depthwise forward's.
-template <int K>
-struct UpShape {
-  using G = Geo<K>;
-  static constexpr int TH = kWarps * 8;
-  static constexpr int ROWS = TH + 2 * G::R;
-  static constexpr int SRC_ROWS = ROWS / 2 + 2;                // input rows under the window (s >= 2)
-  static constexpr int SRC_COLS = round_up(G::SP / 2 + 2, 4);  // input columns (pitch)
-  static constexpr int STAGE = round_up(G::WPAD, 4) + SRC_ROWS * SRC_COLS;  // filter + pixels
-  static constexpr int TABLES = G::SP + 2 * round_up(ROWS, 4);  // column map, row tables
-  static constexpr int SM_FLOATS_1 = ROWS * G::SP + TABLES + STAGE;  // one tile per CTA
-  static constexpr int SM_FLOATS = SM_FLOATS_1 + STAGE;               // two stages
-};
-
 // One 64 x 128 output tile of the upsampled grid at a time per CTA (8 warps,
 // 8 rows each), over tiles t = blockIdx.x, + gridDim.x, ... (launched with one
 // tile per CTA: measured faster than persistent CTAs, which need a second
@@ -105,11 +63,7 @@ struct UpShape {
 // its halo window needs (rows and columns of the upsampled window divided by
 // s, clamped to the image) and its plane's filter are copied to one of two
 // stages -- those of the next tile are copied while this one is computed --
-// then every shared cell (sr, sc) of the FP32 halo tile, upsampled pixel
-// (u, v) = (ty0 - r + sr, tx0 - RP + sc), takes the border rule on the
-// upsampled image (zero: the cell is 0; clamp: (u, v) clamped) and reads the
-// copied input pixel (u / s, v / s).  The forward loop and the store are the
-// depthwise forward's.
+// then up_tile expands them along the columns and filters the tile.
 template <typename T, int K>
 __global__ void __launch_bounds__(kThreads) up_fwd_kernel(const T* __restrict__ x,
                                                           const float* __restrict__ w,
@@ -119,16 +73,13 @@ __global__ void __launch_bounds__(kThreads) up_fwd_kernel(const T* __restrict__ 
                                                           int clamp, int vec) {
   using G = Geo<K>;
   using U = UpShape<K>;
-  constexpr int PY = 8;
   extern __shared__ __align__(16) float smem[];
-  float* st = smem;                                 // ROWS x SP halo tile
-  int* scol = reinterpret_cast<int*>(st + U::ROWS * G::SP);  // SP column map
-  int* srow_of = scol + G::SP;                      // ROWS: input row of each halo row
-  int* slead = srow_of + round_up(U::ROWS, 4);      // ROWS: first row of its run
+  float* sx = smem;                                  // expanded input rows + a zero row
+  int* scol = reinterpret_cast<int*>(sx + U::EXP);   // SP column map
+  int* rowoff = scol + G::SP;                        // ROWS: offset of each halo row in sx
   // 1 or 2 x {filter, SRC_ROWS x SRC_COLS pixels}; the second only when a CTA
   // runs several tiles
   float* stages = reinterpret_cast<float*>(scol) + U::TABLES;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   struct Tile {
     int ty0, tx0, su0, sv0, nr, nc;
@@ -157,30 +108,8 @@ __global__ void __launch_bounds__(kThreads) up_fwd_kernel(const T* __restrict__ 
     float* sw = stages + b * U::STAGE;
     float* ss = sw + round_up(G::WPAD, 4);
     stage_filter_async<K>(sw, w + (int64_t)(tl.plane % C) * K * K, false, kThreads);
-    const T* xp = x + tl.plane * (int64_t)H * W;
-    const int n = tl.nr * tl.nc;
-    if constexpr (sizeof(T) == 4) {
-      for (int k = threadIdx.x; k < n; k += kThreads) {
-        const int r = k / tl.nc, c = k - (k / tl.nc) * tl.nc;
-        cp_async4(ss + r * U::SRC_COLS + c, xp + (int64_t)(tl.su0 + r) * W + tl.sv0 + c, true);
-      }
-    } else {
-      constexpr int PER = (U::SRC_ROWS * U::SRC_COLS + kThreads - 1) / kThreads;
-      float v[PER];
-#pragma unroll
-      for (int i = 0; i < PER; ++i) {
-        const int k = i * kThreads + threadIdx.x;
-        if (k < n) {
-          const int r = k / tl.nc, c = k - (k / tl.nc) * tl.nc;
-          v[i] = Elem<T>::load(xp + (int64_t)(tl.su0 + r) * W + tl.sv0 + c);
-        }
-      }
-#pragma unroll
-      for (int i = 0; i < PER; ++i) {
-        const int k = i * kThreads + threadIdx.x;
-        if (k < n) ss[(k / tl.nc) * U::SRC_COLS + (k - (k / tl.nc) * tl.nc)] = v[i];
-      }
-    }
+    const T* xp = x + tl.plane * (int64_t)H * W + (int64_t)tl.su0 * W + tl.sv0;
+    up_stage_pixels<T, U::SRC_ROWS * U::SRC_COLS>(ss, U::SRC_COLS, xp, W, tl.nr, tl.nc);
     cp_async_commit();
   };
 
@@ -188,6 +117,7 @@ __global__ void __launch_bounds__(kThreads) up_fwd_kernel(const T* __restrict__ 
   if (t >= num_tiles) return;
   Tile cur = locate(t);
   stage(cur, 0);
+  for (int k = threadIdx.x; k < G::SP; k += kThreads) sx[U::ZERO_OFF + k] = 0.f;
   for (int b = 0; t < num_tiles; t += gridDim.x, b ^= 1) {
     const int64_t tn = t + gridDim.x;
     Tile nxt;
@@ -200,67 +130,9 @@ __global__ void __launch_bounds__(kThreads) up_fwd_kernel(const T* __restrict__ 
     }
     const float* sw = stages + b * U::STAGE;
     const float* ss = sw + round_up(G::WPAD, 4);
-    // Expand.  The column mapping is the same for every row: scol[sc] is the
-    // copied input column of halo column sc (-1: zero border, outside).  Halo
-    // rows come in runs that read the same input row (srow_of; -1: zero
-    // border, outside): the first row of a run (slead) is built from the
-    // copied pixels, the others copy it.
-    const int ty0 = cur.ty0, tx0 = cur.tx0, su0 = cur.su0, sv0 = cur.sv0;
-    auto src_row = [&](int sr) {
-      int u = ty0 - G::R + sr;
-      if (u < 0 || u >= Ho) {
-        if (!clamp) return -1;
-        u = u < 0 ? 0 : Ho - 1;
-      }
-      return (int)fdiv((uint32_t)u, fs) - su0;
-    };
-    for (int sc = threadIdx.x; sc < G::SP; sc += kThreads) {
-      int v = tx0 - G::RP + sc;
-      int m = -1;
-      if (clamp || (v >= 0 && v < Wo)) {
-        v = v < 0 ? 0 : (v >= Wo ? Wo - 1 : v);
-        m = (int)fdiv((uint32_t)v, fs) - sv0;
-      }
-      scol[sc] = m;
-    }
-    for (int sr = threadIdx.x; sr < U::ROWS; sr += kThreads) {
-      const int j = src_row(sr);
-      int lead = sr;
-      while (lead > 0 && src_row(lead - 1) == j) --lead;
-      srow_of[sr] = j;
-      slead[sr] = lead;
-    }
-    cta_barrier();  // copies of this tile landed; tables ready
-    constexpr int CPR = G::SP / 4;
-    for (int k = threadIdx.x; k < U::ROWS * CPR; k += kThreads) {
-      const int sr = k / CPR, sc = (k - (k / CPR) * CPR) * 4;
-      if (slead[sr] != sr) continue;
-      const int j = srow_of[sr];
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (j >= 0) {
-        const int4 m = *reinterpret_cast<const int4*>(scol + sc);
-        const float* srow = ss + j * U::SRC_COLS;
-        v.x = m.x >= 0 ? srow[m.x] : 0.f;
-        v.y = m.y >= 0 ? srow[m.y] : 0.f;
-        v.z = m.z >= 0 ? srow[m.z] : 0.f;
-        v.w = m.w >= 0 ? srow[m.w] : 0.f;
-      }
-      *reinterpret_cast<float4*>(st + sr * G::SP + sc) = v;
-    }
-    cta_barrier();
-    for (int k = threadIdx.x; k < U::ROWS * CPR; k += kThreads) {
-      const int sr = k / CPR, sc = (k - (k / CPR) * CPR) * 4;
-      const int lead = slead[sr];
-      if (lead != sr)
-        *reinterpret_cast<float4*>(st + sr * G::SP + sc) =
-            *reinterpret_cast<const float4*>(st + lead * G::SP + sc);
-    }
-    cta_barrier();
-    float acc[PY][4];
-    fwd_block<K, PY, float>(st + warp * PY * G::SP + 4 * lane, sw, acc);
-    store_block<T, PY>(y + cur.plane * (int64_t)Ho * Wo, Ho, Wo, ty0 + warp * PY,
-                       tx0 + 4 * lane, vec != 0, acc);
-    cta_barrier();  // the halo tile, tables and stage b are free again
+    up_tile<T, K>(sx, U::ZERO_OFF, scol, rowoff, sw, ss, U::SRC_COLS, cur.ty0, cur.tx0, cur.su0,
+                  cur.sv0, cur.nr, Ho, Wo, fs, clamp != 0, y + cur.plane * (int64_t)Ho * Wo,
+                  vec != 0);
     cur = nxt;
   }
 }

@@ -23,6 +23,12 @@ photographs are not available, so uniform [0, 1) pixels stand in for them.
                 BF16 upstream gradient normal(0, 1).
   dense         8 x 1024 x 1024 x 64 BF16 NHWC images, 64 x 3 x 3 x 64 BF16
                 filters normal(0, 0.05), BF16 upstream gradient normal(0, 1).
+  up_ragged     a "photo database" for the sharpening benchmark (Section 6.6
+                run over a batch, the goal of Section 5): 128 three-channel
+                FP32 images, H and W uniform integers in [64, 1024], each
+                upsampled by its own integer scale uniform in [2, 8] and
+                filtered with its own filters of size drawn from {3, 5, 9, 11},
+                normal(0, 0.1), zero border.
 
 Every generator takes size overrides so that tests can draw the same
 distributions at sizes the oracle finishes in seconds.
@@ -34,7 +40,8 @@ from dataclasses import dataclass, field
 import torch
 
 BASE_SEED = 2504
-SEEDS = {"plain_small": 0, "plain_scale": 1, "train": 2, "ragged": 3, "bf16": 4, "dense": 5}
+SEEDS = {"plain_small": 0, "plain_scale": 1, "train": 2, "ragged": 3, "bf16": 4, "dense": 5,
+         "up_ragged": 7}
 
 
 def generator(name: str, salt: int = 0, device: str = "cpu") -> torch.Generator:
@@ -116,6 +123,27 @@ def ragged(n: int = 256, C: int = 3, lo: int = 64, hi: int = 4096, ks=(3, 5, 9, 
         dy = normal((1, C, h, w_), 1.0, g, device, dtype)
         out.append(RaggedImage(h, w_, k, x, w, dy))
     return out
+
+
+def up_ragged_shapes(n: int = 128, lo: int = 64, hi: int = 1024, scales=(2, 8),
+                     ks=(3, 5, 9, 11)):
+    """The (H, W, scale, K) list of the upsampling database, drawn from its seed."""
+    g = generator("up_ragged")
+    H = torch.randint(lo, hi + 1, (n,), generator=g)
+    W = torch.randint(lo, hi + 1, (n,), generator=g)
+    S = torch.randint(scales[0], scales[1] + 1, (n,), generator=g)
+    Ki = torch.randint(0, len(ks), (n,), generator=g)
+    return [(int(h), int(w), int(s), int(ks[int(k)])) for h, w, s, k in zip(H, W, S, Ki)]
+
+
+def up_ragged_image(idx: int, H: int, W: int, K: int, C: int = 3, device: str = "cpu",
+                    dtype=torch.float32):
+    """Image idx of the upsampling database: x (C, H, W) uniform [0, 1) and
+    w (C, K, K) normal(0, 0.1), from the image's own sub-seed."""
+    g = generator("up_ragged", salt=idx + 1, device=device)
+    x = uniform((C, H, W), g, device, dtype)
+    w = normal((C, K, K), 0.1, g, device)
+    return x, w
 
 
 def bf16(N: int = 32, C: int = 3, H: int = 2048, W: int = 2048, K: int = 9,
