@@ -17,6 +17,33 @@ constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kTileW = 128;
 
+// Unsigned division by a fixed divisor d >= 1 as a multiply-high and a shift:
+// with 2^(l-1) < d <= 2^l, mul = ceil(2^(31+l) / d) < 2^32 exceeds 2^(31+l) / d
+// by e / d, e < d <= 2^l, so n * e < 2^(31+l) and the quotient is exact for
+// every n < 2^31.  Tile and plane indices are split this way instead of by
+// 64-bit division, which the compiler emulates with a long instruction
+// sequence.
+struct FastDiv {
+  uint32_t mul, shift, d;
+};
+
+inline FastDiv make_fastdiv(uint32_t d) {
+  FastDiv f{0, 0, d};
+  if (d <= 1) {
+    f.d = 1;
+    return f;
+  }
+  uint32_t l = 0;
+  while ((1ull << l) < d) ++l;
+  f.shift = l - 1;
+  f.mul = (uint32_t)((((uint64_t)1 << (32 + f.shift)) + d - 1) / d);
+  return f;
+}
+
+__device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv& f) {
+  return f.d == 1 ? n : (__umulhi(n, f.mul) >> f.shift);
+}
+
 // Depthwise problem as seen by the launchers (all pointers device memory).
 struct DwArgs {
   const void* x;

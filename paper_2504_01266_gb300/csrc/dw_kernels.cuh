@@ -625,8 +625,8 @@ struct FwdShape {
 template <typename T, int K, int PY>
 __global__ void __launch_bounds__(kThreads) dw_fwd_kernel(
     const __grid_constant__ CUtensorMap tmx, const T* __restrict__ x, const float* __restrict__ w,
-    T* __restrict__ y, int C, int H, int W, int tiles_x, int tiles_y, int64_t num_tiles, int clamp,
-    int vec, int flip, int use_tma, int* err) {
+    T* __restrict__ y, FastDiv fc, int H, int W, FastDiv ftx, FastDiv fty, int64_t num_tiles,
+    int clamp, int vec, int flip, int use_tma, int* err) {
   using G = Geo<K>;
   using GS = Geo<K, sizeof(T)>;
   using S = FwdShape<K, PY, T>;
@@ -638,29 +638,32 @@ __global__ void __launch_bounds__(kThreads) dw_fwd_kernel(
   volatile int* s_abort = reinterpret_cast<volatile int*>(sm + 16);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-  auto coords = [&](int64_t t, int& ty0, int& tx0, int64_t& plane) {
-    tx0 = (int)(t % tiles_x) * kTileW;
-    const int64_t t2 = t / tiles_x;
-    ty0 = (int)(t2 % tiles_y) * TH;
-    plane = t2 / tiles_y;
+  // tile t (< 2^31) -> column and row of the tile, plane (n * C + c)
+  auto coords = [&](int64_t t, int& ty0, int& tx0, int& plane) {
+    const uint32_t u = (uint32_t)t;
+    const uint32_t r = fdiv(u, ftx);
+    tx0 = (int)(u - r * ftx.d) * kTileW;
+    const uint32_t pl = fdiv(r, fty);
+    ty0 = (int)(r - pl * fty.d) * TH;
+    plane = (int)pl;
   };
   auto stage = [&](int64_t t, int sb) {
-    int ty0, tx0;
-    int64_t plane;
+    int ty0, tx0, plane;
     coords(t, ty0, tx0, plane);
     char* buf = sm + S::HEAD + sb * S::STAGE_BYTES;
     T* staged = reinterpret_cast<T*>(buf + ST::STAGE_OFF);
     float* sw = reinterpret_cast<float*>(buf + S::W_OFF);
-    stage_filter_async<K>(sw, w + (int64_t)(plane % C) * K * K, flip != 0, kThreads);
+    const int c = plane - (int)(fdiv((uint32_t)plane, fc) * fc.d);
+    stage_filter_async<K>(sw, w + (int64_t)c * K * K, flip != 0, kThreads);
     if (use_tma) {
       cp_async_commit();
       if (threadIdx.x == 0) {
         fence_proxy_async();
         mbar_expect_tx(bars + sb, (uint32_t)ST::STAGE_BYTES);
-        tma_load_3d(staged, &tmx, tx0 - GS::RP, ty0 - G::R, (int)plane, bars + sb);
+        tma_load_3d(staged, &tmx, tx0 - GS::RP, ty0 - G::R, plane, bars + sb);
       }
     } else {
-      stage_tile<T, G::R, GS::RP, GS::SP>(staged, x + plane * (int64_t)H * W, H, W, ty0, tx0,
+      stage_tile<T, G::R, GS::RP, GS::SP>(staged, x + (int64_t)plane * H * W, H, W, ty0, tx0,
                                           S::ROWS, clamp != 0, vec != 0);
     }
   };
@@ -694,8 +697,7 @@ __global__ void __launch_bounds__(kThreads) dw_fwd_kernel(
     }
     cta_barrier();
     if (*s_abort) break;
-    int ty0, tx0;
-    int64_t plane;
+    int ty0, tx0, plane;
     coords(t, ty0, tx0, plane);
     char* buf = sm + S::HEAD + sb * S::STAGE_BYTES;
     float* sx = reinterpret_cast<float*>(buf);
@@ -708,7 +710,7 @@ __global__ void __launch_bounds__(kThreads) dw_fwd_kernel(
       clamp_fix<float, G::SP, kThreads>(sx, H, W, ty0, tx0, G::R, G::RP, S::ROWS);
     float acc[PY][4];
     fwd_block<K, PY, float>(sx + warp * PY * G::SP + 4 * lane, sw, acc);
-    store_block<T, PY>(y + plane * (int64_t)H * W, H, W, ty0 + warp * PY, tx0 + 4 * lane,
+    store_block<T, PY>(y + (int64_t)plane * H * W, H, W, ty0 + warp * PY, tx0 + 4 * lane,
                        vec != 0, acc);
     cta_barrier();  // every warp is done with stage sb before it is refilled
   }
@@ -741,8 +743,8 @@ struct SepShape {
 template <typename T, int K>
 __global__ void __launch_bounds__(kThreads) dw_sep_kernel(
     const __grid_constant__ CUtensorMap tmx, const T* __restrict__ x,
-    const float* __restrict__ wcol, const float* __restrict__ wrow, T* __restrict__ y, int C,
-    int H, int W, int tiles_x, int tiles_y, int clamp, int vec, int use_tma, int* err) {
+    const float* __restrict__ wcol, const float* __restrict__ wrow, T* __restrict__ y, FastDiv fc,
+    int H, int W, FastDiv ftx, FastDiv fty, int clamp, int vec, int use_tma, int* err) {
   using G = Geo<K>;
   using GS = Geo<K, sizeof(T)>;
   using S = SepShape<K, T>;
@@ -755,12 +757,13 @@ __global__ void __launch_bounds__(kThreads) dw_sep_kernel(
   float* swr = reinterpret_cast<float*>(sm + S::W_OFF);
   float* swc = swr + KP;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t t = blockIdx.x;
-  const int tx0 = (int)(t % tiles_x) * kTileW;
-  const int64_t t2 = t / tiles_x;
-  const int ty0 = (int)(t2 % tiles_y) * S::TH;
-  const int64_t plane = t2 / tiles_y;
-  const int c = (int)(plane % C);
+  const uint32_t t = blockIdx.x;
+  const uint32_t t2 = fdiv(t, ftx);
+  const int tx0 = (int)(t - t2 * ftx.d) * kTileW;
+  const uint32_t pl = fdiv(t2, fty);
+  const int ty0 = (int)(t2 - pl * fty.d) * S::TH;
+  const int plane = (int)pl;
+  const int c = (int)(pl - fdiv(pl, fc) * fc.d);
 
   for (int k = threadIdx.x; k < 2 * KP; k += kThreads) {
     const int b = k < KP ? k : k - KP;
@@ -780,7 +783,7 @@ __global__ void __launch_bounds__(kThreads) dw_sep_kernel(
     if (threadIdx.x == 0) {
       fence_proxy_async();
       mbar_expect_tx(bar, (uint32_t)ST::STAGE_BYTES);
-      tma_load_3d(staged, &tmx, tx0 - GS::RP, ty0 - G::R, (int)plane, bar);
+      tma_load_3d(staged, &tmx, tx0 - GS::RP, ty0 - G::R, plane, bar);
     }
     cp_async_wait_all();
     if (!mbar_wait(bar, 0)) {
@@ -788,7 +791,7 @@ __global__ void __launch_bounds__(kThreads) dw_sep_kernel(
       *s_abort = 1;
     }
   } else {
-    stage_tile<T, G::R, GS::RP, GS::SP>(staged, x + plane * (int64_t)H * W, H, W, ty0, tx0,
+    stage_tile<T, G::R, GS::RP, GS::SP>(staged, x + (int64_t)plane * H * W, H, W, ty0, tx0,
                                         S::ROWS, clamp != 0, vec != 0);
     cp_async_wait_all();
   }
@@ -841,7 +844,7 @@ __global__ void __launch_bounds__(kThreads) dw_sep_kernel(
       }
     }
   }
-  store_block<T, PY>(y + plane * (int64_t)H * W, H, W, ty0 + warp * PY, tx0 + 4 * lane,
+  store_block<T, PY>(y + (int64_t)plane * H * W, H, W, ty0 + warp * PY, tx0 + 4 * lane,
                      vec != 0, acc);
 }
 
@@ -909,12 +912,12 @@ __global__ void __launch_bounds__(kThreads, bwd_min_ctas<T, K>())
   float* sm_w = reinterpret_cast<float*>(sm + S::SM_W);
   float* sm_red = reinterpret_cast<float*>(sm + S::SM_RED);
 
-  const int64_t plane = blockIdx.x / chunks_per_plane;
-  const int chunk = blockIdx.x % chunks_per_plane;
+  const int plane = (int)(blockIdx.x / (uint32_t)chunks_per_plane);
+  const int chunk = (int)(blockIdx.x - (uint32_t)plane * chunks_per_plane);
   const int t_begin = chunk * tpc;
   const int t_end = min(t_begin + tpc, tiles_per_plane);
-  const int c = (int)(plane % C);
-  const int64_t plane_off = plane * (int64_t)H * W;
+  const int c = plane % C;
+  const int64_t plane_off = (int64_t)plane * H * W;
   const T* xp = x + plane_off;
   const T* dyp = dy + plane_off;
 
@@ -1091,8 +1094,8 @@ __global__ void __launch_bounds__(FilterShape<K, T>::NT, 1)
     dw_filter_kernel(const __grid_constant__ CUtensorMap tmx,
                      const __grid_constant__ CUtensorMap tmdy, const T* __restrict__ x,
                      const T* __restrict__ dy, float* __restrict__ partials, int H, int W,
-                     int tiles_x, int tiles_per_plane, int chunks_per_plane, int tpc,
-                     int64_t num_chunks, int clamp, int vec, int use_tma, int* err) {
+                     FastDiv ftx, int tiles_per_plane, FastDiv fcpp, int tpc, int num_chunks,
+                     int clamp, int vec, int use_tma, int* err) {
   using G = Geo<K, sizeof(T)>;
   using S = FilterShape<K, T>;
   extern __shared__ __align__(128) float smem[];
@@ -1106,12 +1109,19 @@ __global__ void __launch_bounds__(FilterShape<K, T>::NT, 1)
   const int nrows = group_lo(g + 1, K, S::GT) - a_lo;
 
   // (chunk, tile) items in execution order; t < t_end while valid
+  // chunk q < 2^31 of plane q / chunks_per_plane; tile t of that plane is
+  // tile row t / tiles_x, column t % tiles_x
   struct Item {
-    int64_t q;
+    int q;
     int t, t_end;
   };
+  auto tile_origin = [&](int t, int& ty0, int& tx0) {
+    const uint32_t r = fdiv((uint32_t)t, ftx);
+    ty0 = (int)r * kFilterTileH;
+    tx0 = (t - (int)(r * ftx.d)) * kTileW;
+  };
   auto first_tile = [&](Item& it) {
-    const int ch = (int)(it.q % chunks_per_plane);
+    const int ch = it.q - (int)(fdiv((uint32_t)it.q, fcpp) * fcpp.d);
     it.t = ch * tpc;
     it.t_end = min(it.t + tpc, tiles_per_plane);
   };
@@ -1123,24 +1133,26 @@ __global__ void __launch_bounds__(FilterShape<K, T>::NT, 1)
   };
   // the x halo of a tile reaches outside the image (same answer for every thread)
   auto at_edge = [&](const Item& it) {
-    const int ty0 = (it.t / tiles_x) * kFilterTileH, tx0 = (it.t % tiles_x) * kTileW;
+    int ty0, tx0;
+    tile_origin(it.t, ty0, tx0);
     return ty0 - G::R < 0 || ty0 + kFilterTileH + G::R > H || tx0 - G::RP < 0 ||
            tx0 + kTileW + G::RP > W;
   };
   auto stage = [&](const Item& it, int sb) {
-    const int64_t plane = it.q / chunks_per_plane;
-    const int ty0 = (it.t / tiles_x) * kFilterTileH, tx0 = (it.t % tiles_x) * kTileW;
+    const int plane = (int)fdiv((uint32_t)it.q, fcpp);
+    int ty0, tx0;
+    tile_origin(it.t, ty0, tx0);
     T* sx = reinterpret_cast<T*>(sm + sb * S::STAGE_BYTES);
     T* sdy = reinterpret_cast<T*>(sm + sb * S::STAGE_BYTES + S::DY_OFF);
     if (use_tma) {
       if (threadIdx.x == 0) {
         fence_proxy_async();
         mbar_expect_tx(bars + sb, (uint32_t)(S::X_BYTES + S::DY_BYTES));
-        tma_load_3d(sx, &tmx, tx0 - G::RP, ty0 - G::R, (int)plane, bars + sb);
-        tma_load_3d(sdy, &tmdy, tx0, ty0, (int)plane, bars + sb);
+        tma_load_3d(sx, &tmx, tx0 - G::RP, ty0 - G::R, plane, bars + sb);
+        tma_load_3d(sdy, &tmdy, tx0, ty0, plane, bars + sb);
       }
     } else {
-      const int64_t off = plane * (int64_t)H * W;
+      const int64_t off = (int64_t)plane * H * W;
       stage_tile<T, G::R, G::RP, G::SP, S::NT, false>(sx, x + off, H, W, ty0, tx0, S::X_ROWS,
                                                       clamp != 0, vec != 0);
       stage_tile<T, 0, 0, kTileW, S::NT, false>(sdy, dy + off, H, W, ty0, tx0, kFilterTileH,
@@ -1155,7 +1167,7 @@ __global__ void __launch_bounds__(FilterShape<K, T>::NT, 1)
   }
   cta_barrier();
 
-  Item pf{(int64_t)blockIdx.x, 0, 0};
+  Item pf{(int)blockIdx.x, 0, 0};
   if (pf.q >= num_chunks) return;
   first_tile(pf);
   Item cs = pf;
@@ -1200,9 +1212,11 @@ __global__ void __launch_bounds__(FilterShape<K, T>::NT, 1)
     if (*s_abort) break;
     T* sx = reinterpret_cast<T*>(sm + sb * S::STAGE_BYTES);
     const T* sdy = reinterpret_cast<const T*>(sm + sb * S::STAGE_BYTES + S::DY_OFF);
-    if (use_tma && clamp && at_edge(cs))
-      clamp_fix<T, G::SP, S::NT>(sx, H, W, (cs.t / tiles_x) * kFilterTileH,
-                                 (cs.t % tiles_x) * kTileW, G::R, G::RP, S::X_ROWS);
+    if (use_tma && clamp && at_edge(cs)) {
+      int ty0, tx0;
+      tile_origin(cs.t, ty0, tx0);
+      clamp_fix<T, G::SP, S::NT>(sx, H, W, ty0, tx0, G::R, G::RP, S::X_ROWS);
+    }
     dw_rows<K, S::AT, S::GT, kTileW, S::DR, T>(sdy + part * S::ROWS * kTileW + 4 * lane,
                                                sx + (part * S::ROWS + a_lo) * G::SP + 4 * lane,
                                                S::ROWS / S::DR, nrows, acc);
@@ -1228,7 +1242,7 @@ __global__ void __launch_bounds__(FilterShape<K, T>::NT, 1)
         const int s = a - group_lo(gg, K, S::GT);
         float sum = 0.f;
         for (int p = 0; p < S::WPG; ++p) sum += sm_red[((gg * S::WPG + p) * S::AT + s) * K + b];
-        partials[cs.q * K * K + k] = sum;
+        partials[(int64_t)cs.q * K * K + k] = sum;
       }
       // sm_red is rewritten no earlier than the next chunk end, after another barrier
     }

@@ -41,7 +41,7 @@ static cudaError_t fwd_impl(const DwArgs& a, bool input_grad, bool persistent, c
     }
     grid = std::min<int64_t>(tiles, (int64_t)per_sm * sm_count());
   }
-  if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  if (tiles > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
   const T* in = static_cast<const T*>(input_grad ? a.dy : a.x);
   T* out = static_cast<T*>(input_grad ? a.dx : a.y);
   // TMA staging for rows with a 16-byte stride from a 16-byte aligned base
@@ -51,10 +51,10 @@ static cudaError_t fwd_impl(const DwArgs& a, bool input_grad, bool persistent, c
   if (plane_tma_ok(in, sizeof(T), a.W))
     use_tma = make_plane_map(&tm, in, sizeof(T), a.W, a.H, a.N * a.C, Geo<K, sizeof(T)>::SP,
                              S::ROWS);
-  kern<<<(unsigned)grid, kThreads, smem, st>>>(tm, in, a.w, out, (int)a.C, (int)a.H, (int)a.W,
-                                               (int)tiles_x, (int)tiles_y, tiles,
-                                               input_grad ? 0 : a.border, a.vec,
-                                               input_grad ? 1 : 0, use_tma, dw_error_word());
+  kern<<<(unsigned)grid, kThreads, smem, st>>>(
+      tm, in, a.w, out, make_fastdiv((uint32_t)a.C), (int)a.H, (int)a.W,
+      make_fastdiv((uint32_t)tiles_x), make_fastdiv((uint32_t)tiles_y), tiles,
+      input_grad ? 0 : a.border, a.vec, input_grad ? 1 : 0, use_tma, dw_error_word());
   note_launch();
   return cudaGetLastError();
 }
@@ -132,6 +132,7 @@ static cudaError_t filter_impl(const DwArgs& a, const DwConfig& cfg, cudaStream_
   const int64_t chunks = dw_bwd_chunks_per_plane(a.H, a.W, cfg.tiles_per_cta);
   const int64_t num_chunks = a.N * a.C * chunks;
   const int64_t grid = std::min<int64_t>(num_chunks, (int64_t)per_sm * sm_count());
+  if (num_chunks + grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
   // TMA staging: rows with a 16-byte stride from 16-byte aligned bases;
   // otherwise cp.async staging.
   CUtensorMap tmx, tmdy;
@@ -146,8 +147,9 @@ static cudaError_t filter_impl(const DwArgs& a, const DwConfig& cfg, cudaStream_
   int* err = dw_error_word();
   kern<<<(unsigned)grid, S::NT, smem, st>>>(
       tmx, tmdy, static_cast<const T*>(a.x), static_cast<const T*>(a.dy), a.partials, (int)a.H,
-      (int)a.W, (int)tiles_x, (int)(tiles_x * tiles_y), (int)chunks, cfg.tiles_per_cta,
-      num_chunks, a.border, a.vec, use_tma, err);
+      (int)a.W, make_fastdiv((uint32_t)tiles_x), (int)(tiles_x * tiles_y),
+      make_fastdiv((uint32_t)chunks), cfg.tiles_per_cta, (int)num_chunks, a.border, a.vec,
+      use_tma, err);
   note_launch();
   return cudaGetLastError();
 }
@@ -179,8 +181,9 @@ static cudaError_t sep_impl(const DwArgs& a, const float* wcol, const float* wro
     use_tma = make_plane_map(&tm, a.x, sizeof(T), a.W, a.H, a.N * a.C, Geo<K, sizeof(T)>::SP,
                              S::ROWS);
   dw_sep_kernel<T, K><<<(unsigned)grid, kThreads, (size_t)S::SM_BYTES, st>>>(
-      tm, static_cast<const T*>(a.x), wcol, wrow, static_cast<T*>(a.y), (int)a.C, (int)a.H,
-      (int)a.W, (int)tiles_x, (int)tiles_y, a.border, a.vec, use_tma, dw_error_word());
+      tm, static_cast<const T*>(a.x), wcol, wrow, static_cast<T*>(a.y),
+      make_fastdiv((uint32_t)a.C), (int)a.H, (int)a.W, make_fastdiv((uint32_t)tiles_x),
+      make_fastdiv((uint32_t)tiles_y), a.border, a.vec, use_tma, dw_error_word());
   note_launch();
   return cudaGetLastError();
 }

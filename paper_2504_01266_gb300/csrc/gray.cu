@@ -64,7 +64,7 @@ struct GrayShape {
 template <typename T, int K>
 __global__ void __launch_bounds__(kThreads) gray_fwd_kernel(
     const __grid_constant__ CUtensorMap tmx, const T* __restrict__ x, const float* __restrict__ w,
-    T* __restrict__ y, int H, int W, int tiles_x, int tiles_y, int clamp, int vec, int use_tma,
+    T* __restrict__ y, int H, int W, FastDiv ftx, FastDiv fty, int clamp, int vec, int use_tma,
     int* err) {
   using G = Geo<K>;
   using GS = Geo<K, sizeof(T)>;
@@ -77,11 +77,12 @@ __global__ void __launch_bounds__(kThreads) gray_fwd_kernel(
   float* gt = reinterpret_cast<float*>(sm + S::GRAY);
   float* sw = reinterpret_cast<float*>(sm + S::W_OFF);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t t = blockIdx.x;
-  const int tx0 = (int)(t % tiles_x) * kTileW;
-  const int64_t t2 = t / tiles_x;
-  const int ty0 = (int)(t2 % tiles_y) * S::TH;
-  const int64_t n = t2 / tiles_y;
+  const uint32_t t = blockIdx.x;
+  const uint32_t t2 = fdiv(t, ftx);
+  const int tx0 = (int)(t - t2 * ftx.d) * kTileW;
+  const uint32_t nu = fdiv(t2, fty);
+  const int ty0 = (int)(t2 - nu * fty.d) * S::TH;
+  const int64_t n = nu;
 
   stage_filter_async<K>(sw, w, false, kThreads);
   if (threadIdx.x == 0) {
@@ -174,7 +175,8 @@ static cudaError_t gray_fwd_impl(const GrayArgs& a, cudaStream_t st) {
   }
   gray_fwd_kernel<T, K><<<(unsigned)grid, kThreads, (size_t)S::SM_BYTES, st>>>(
       tm, static_cast<const T*>(a.x), a.w, static_cast<T*>(a.y), (int)a.H, (int)a.W,
-      (int)tiles_x, (int)tiles_y, a.border, a.vec, use_tma, dw_error_word());
+      make_fastdiv((uint32_t)tiles_x), make_fastdiv((uint32_t)tiles_y), a.border, a.vec, use_tma,
+      dw_error_word());
   note_launch();
   return cudaGetLastError();
 }

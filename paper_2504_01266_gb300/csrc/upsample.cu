@@ -67,10 +67,10 @@ __global__ void __launch_bounds__(256) up_nearest_kernel(const T* __restrict__ x
 template <typename T, int K>
 __global__ void __launch_bounds__(kThreads) up_fwd_kernel(const T* __restrict__ x,
                                                           const float* __restrict__ w,
-                                                          T* __restrict__ y, int C, int H, int W,
-                                                          int Ho, int Wo, FastDiv fs, int tiles_x,
-                                                          int tiles_y, int64_t num_tiles,
-                                                          int clamp, int vec) {
+                                                          T* __restrict__ y, FastDiv fc, int H,
+                                                          int W, int Ho, int Wo, FastDiv fs,
+                                                          FastDiv ftx, FastDiv fty,
+                                                          int64_t num_tiles, int clamp, int vec) {
   using G = Geo<K>;
   using U = UpShape<K>;
   extern __shared__ __align__(16) float smem[];
@@ -83,14 +83,16 @@ __global__ void __launch_bounds__(kThreads) up_fwd_kernel(const T* __restrict__ 
 
   struct Tile {
     int ty0, tx0, su0, sv0, nr, nc;
-    int64_t plane;
+    int plane;
   };
-  auto locate = [&](int64_t t) {
+  auto locate = [&](int64_t t) {  // t < 2^31
     Tile tl;
-    tl.tx0 = (int)(t % tiles_x) * kTileW;
-    const int64_t t2 = t / tiles_x;
-    tl.ty0 = (int)(t2 % tiles_y) * U::TH;
-    tl.plane = t2 / tiles_y;
+    const uint32_t u = (uint32_t)t;
+    const uint32_t t2 = fdiv(u, ftx);
+    tl.tx0 = (int)(u - t2 * ftx.d) * kTileW;
+    const uint32_t pl = fdiv(t2, fty);
+    tl.ty0 = (int)(t2 - pl * fty.d) * U::TH;
+    tl.plane = (int)pl;
     // input window: upsampled rows [ty0 - r, ty0 + TH + r), columns
     // [tx0 - RP, tx0 + 128 + RP), clamped to the upsampled image, divided by s
     const int u_lo = max(tl.ty0 - G::R, 0), u_hi = min(tl.ty0 + U::TH + G::R, Ho) - 1;
@@ -107,8 +109,9 @@ __global__ void __launch_bounds__(kThreads) up_fwd_kernel(const T* __restrict__ 
   auto stage = [&](const Tile& tl, int b) {
     float* sw = stages + b * U::STAGE;
     float* ss = sw + round_up(G::WPAD, 4);
-    stage_filter_async<K>(sw, w + (int64_t)(tl.plane % C) * K * K, false, kThreads);
-    const T* xp = x + tl.plane * (int64_t)H * W + (int64_t)tl.su0 * W + tl.sv0;
+    const int c = tl.plane - (int)(fdiv((uint32_t)tl.plane, fc) * fc.d);
+    stage_filter_async<K>(sw, w + (int64_t)c * K * K, false, kThreads);
+    const T* xp = x + (int64_t)tl.plane * H * W + (int64_t)tl.su0 * W + tl.sv0;
     up_stage_pixels<T, U::SRC_ROWS * U::SRC_COLS>(ss, U::SRC_COLS, xp, W, tl.nr, tl.nc);
     cp_async_commit();
   };
@@ -131,7 +134,7 @@ __global__ void __launch_bounds__(kThreads) up_fwd_kernel(const T* __restrict__ 
     const float* sw = stages + b * U::STAGE;
     const float* ss = sw + round_up(G::WPAD, 4);
     up_tile<T, K>(sx, U::ZERO_OFF, scol, rowoff, sw, ss, U::SRC_COLS, cur.ty0, cur.tx0, cur.su0,
-                  cur.sv0, cur.nr, Ho, Wo, fs, clamp != 0, y + cur.plane * (int64_t)Ho * Wo,
+                  cur.sv0, cur.nr, Ho, Wo, fs, clamp != 0, y + (int64_t)cur.plane * Ho * Wo,
                   vec != 0);
     cur = nxt;
   }
@@ -151,9 +154,9 @@ static cudaError_t up_fwd_impl(const UpArgs& a, cudaStream_t st) {
   const int64_t grid = tiles;  // one tile per CTA: the second stage is never used
   const size_t smem1 = (size_t)U::SM_FLOATS_1 * 4;
   kern<<<(unsigned)grid, kThreads, smem1, st>>>(
-      static_cast<const T*>(a.x), a.w, static_cast<T*>(a.y), (int)a.C, (int)a.H, (int)a.W,
-      (int)a.Ho, (int)a.Wo, make_fastdiv((uint32_t)a.s), (int)tiles_x, (int)tiles_y, tiles,
-      a.border, a.vec);
+      static_cast<const T*>(a.x), a.w, static_cast<T*>(a.y), make_fastdiv((uint32_t)a.C),
+      (int)a.H, (int)a.W, (int)a.Ho, (int)a.Wo, make_fastdiv((uint32_t)a.s),
+      make_fastdiv((uint32_t)tiles_x), make_fastdiv((uint32_t)tiles_y), tiles, a.border, a.vec);
   note_launch();
   return cudaGetLastError();
 }

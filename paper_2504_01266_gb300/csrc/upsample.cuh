@@ -13,26 +13,6 @@
 
 namespace giga {
 
-// Unsigned division by a fixed divisor d >= 1 as a multiply-high and a shift
-// (round-up reciprocal; exact for every n < 2^31).
-struct FastDiv {
-  uint32_t mul, shift, d;
-};
-
-inline FastDiv make_fastdiv(uint32_t d) {
-  FastDiv f{0, 0, d};
-  if (d == 1) return f;
-  uint32_t l = 0;
-  while ((1u << l) < d) ++l;
-  f.shift = l - 1;
-  f.mul = (uint32_t)((((uint64_t)1 << (32 + f.shift)) + d - 1) / d);
-  return f;
-}
-
-__device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv& f) {
-  return f.d == 1 ? n : (__umulhi(n, f.mul) >> f.shift);
-}
-
 // Geometry of one 64 x 128 output tile of the upsampled grid (8 warps, 8 rows
 // each) for a K x K filter and a scale s >= 2: the staged input pixels under
 // the tile's window, the same rows expanded along the columns of the FP32 halo
