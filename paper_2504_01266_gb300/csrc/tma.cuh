@@ -50,20 +50,31 @@ __device__ __forceinline__ uint64_t global_ns() {
   return t;
 }
 
+// Longest time (ns) one try_wait may keep a thread suspended before it
+// returns to the loop; the hardware resumes the thread earlier when the phase
+// completes, so waiting costs no issue slots.
+constexpr uint32_t kSuspendHintNs = 1000000u;
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t a, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(done)
+      : "r"(a), "r"(parity), "r"(kSuspendHintNs)
+      : "memory");
+  return done != 0;
+}
+
 // Wait for the phase with parity `parity` to complete; false after
 // kWaitLimitNs of wall time (the caller then records an error and stops).
+// The clock is read only once the first try_wait has returned unfinished.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   const uint32_t a = s_addr(bar);
+  if (mbar_try_wait(a, parity)) return true;
   const uint64_t t0 = global_ns();
   for (;;) {
-    uint32_t done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        " selp.u32 %0, 1, 0, p;\n}"
-        : "=r"(done)
-        : "r"(a), "r"(parity)
-        : "memory");
-    if (done) return true;
+    if (mbar_try_wait(a, parity)) return true;
     if (global_ns() - t0 > kWaitLimitNs) return false;
   }
 }
