@@ -97,8 +97,6 @@ __device__ __forceinline__ uint32_t kDenseIdescN(int n) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((128u >> 4) << 24);
 }
 
-// Same shape with both operands MN-major (filter gradient).
-constexpr uint32_t kDenseIdescMN = kDenseIdesc | (1u << 15) | (1u << 16);
 
 __device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
                                        uint32_t accumulate) {
@@ -419,30 +417,52 @@ __global__ void __launch_bounds__(kDenseThreads, 1)
 
 // ------------------------------------------------------- filter gradient
 //   dw[o][a][b][c] = sum_{n,i,j} dy[n][i][j][o] * x[n][i + a - 1][j + b - 1][c]
-// For a chunk of 64 pixels of one image row, a TMA load of the shifted x
-// block of tap t is a 64-pixel x 64-channel tile whose 128-byte rows are
-// pixels: read as MN-major it is the K x M operand (K = pixels, M = input
-// channels).  Two taps' tiles placed 8 KB apart form one M = 128 operand
-// (rows 0-63: tap 2q, rows 64-127: tap 2q + 1); the dy tile is the K x N
-// operand (N = output channels).  D[(tap, c)][o] accumulates in TMEM over all
-// pixel chunks of the CTA: 5 tap pairs x 64 columns (the 10th tap slot is a
-// zero tile).  Each CTA then writes its 5 x 128 x 64 FP32 partial sums and a
-// second kernel adds the CTAs' partials in FP64 in CTA order.
-constexpr int kWgTileP = 64;                    // pixels per chunk
-constexpr int kWgTileBytes = kWgTileP * kDenseC * 2;  // 8 KB
-constexpr int kWgSlots = 11;                    // 9 taps + zero tile + dy
-constexpr int kWgStageBytes = kWgSlots * kWgTileBytes;
-constexpr int kWgStages = 2;
-constexpr int kWgPairs = 5;
+// Work unit: a chunk of 64 pixel positions k = 0..63 at j0 + k of one image
+// row i.  Per chunk the producer loads three x bands (image rows i - 1, i,
+// i + 1; pixels j0 - 1 .. j0 + 63, 65 pixels x 64 channels, one 128-byte row
+// per pixel, 128-byte swizzle) and one dy band (row i, pixels j0 - 2 ..
+// j0 + 63), 34.6 KB; six stages are in flight.  Both are read as MN-major
+// operands (K = pixel position), a view b pixels into a band being a start
+// address b * 128 bytes in (the swizzle phase follows the absolute shared
+// address).  With A[k][c] = x[j0 + k - 1][c] (x band of tap row a, view 0)
+// and B_s[k][o] = dy[j0 + k - s][o] (dy band, view 2 - s):
+//   sum_k A[k][c] B_s[k][o] = sum_p x[p + s - 1][c] dy[p][o],  p = j0 + k - s,
+// the contribution of tap (a, s) over the pixels p = j0 - s .. j0 + 63 - s.
+// The chunks of a row (ceil((W + 2) / 64) of them) tile every pixel once for
+// each s (dy is zero outside the image), so one MMA with N = 192 -- B = the
+// three shifts s = 2, 1, 0 as 64-column N blocks 128 bytes apart -- gives all
+// three taps of a filter row, and M = 128 stacks two filter rows (x bands of
+// rows a and a + 1, one band stride apart):
+//   MMA 0: rows a = 0, 1 -> 6 taps;   MMA 1: row a = 2 (the second M half,
+//   band 2 viewed one pixel further, is computed and discarded).
+// 8 MMAs of 128 x 192 x 16 per chunk read 80 KB of operands instead of the
+// 120 KB of 20 MMAs of 128 x 64 x 16 with one tap pair each.  D accumulates in
+// TMEM over all chunks of the CTA (2 x 192 columns); each CTA then writes its
+// FP32 partial sums [tap][c][o] and a second kernel adds the CTAs' partials
+// in FP64 in CTA order.
+constexpr int kWgTileP = 64;                           // pixel positions per chunk (MMA K: 4 x 16)
+constexpr int kWgXPx = kWgTileP + 1;                   // x band: 65 pixels
+constexpr int kWgDyPx = kWgTileP + 2;                  // dy band: 66 pixels
+constexpr int kWgSlot = 9 * 1024;                      // 1024-aligned band slots
+constexpr int kWgDyOff = 3 * kWgSlot;
+constexpr int kWgStageBytes = 4 * kWgSlot;             // 36 KB
+constexpr uint32_t kWgStageTx = (3 * kWgXPx + kWgDyPx) * kDenseC * 2;
+constexpr int kWgStages = 6;
+constexpr int kWgN = 192;                              // three 64-channel shifts
 constexpr int kWgTmemCols = 512;
 constexpr size_t kWgSmem = 1024 + kWgStages * kWgStageBytes + 256;
-constexpr int64_t kWgPartialFloats = (int64_t)kWgPairs * 128 * kDenseC;
+constexpr int64_t kWgPartialFloats = (int64_t)kDenseTaps * kDenseC * kDenseC;
+static_assert(kWgSmem <= 227 * 1024, "filter-gradient shared memory");
+
+// M = 128, N = 192, both operands MN-major.
+constexpr uint32_t kWgIdesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) |
+                              ((uint32_t)(kWgN >> 3) << 17) | ((128u >> 4) << 24);
 
 struct WgParams {
-  float* partials;  // [grid][5][128][64]
+  float* partials;  // [grid][9][64][64]
   int* err;
   int N, H, W;
-  int tiles_w;
+  int tiles_w;      // chunks per row: ceil((W + 2) / 64)
   int64_t num_tiles;
 };
 
@@ -460,11 +480,6 @@ __global__ void __launch_bounds__(kDenseThreads, 1)
   __shared__ volatile int s_abort;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-  // zero tile (slot 9) of every stage: written once, never loaded into
-  for (int st = 0; st < kWgStages; ++st) {
-    uint4* z = reinterpret_cast<uint4*>(smem + st * kWgStageBytes + 9 * kWgTileBytes);
-    for (int k = threadIdx.x; k < kWgTileBytes / 16; k += kDenseThreads) z[k] = make_uint4(0, 0, 0, 0);
-  }
   if (threadIdx.x == 0) {
     s_abort = 0;
     for (int st = 0; st < kWgStages; ++st) {
@@ -474,8 +489,6 @@ __global__ void __launch_bounds__(kDenseThreads, 1)
     mbar_init(done, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  // make the generic-proxy zero tiles visible to the tensor cores
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      s_addr(tmem_slot)),
@@ -502,11 +515,10 @@ __global__ void __launch_bounds__(kDenseThreads, 1)
           break;
         }
         uint8_t* base = smem + stage * kWgStageBytes;
-        mbar_expect_tx(full + stage, 10 * kWgTileBytes);
-        for (int t = 0; t < kDenseTaps; ++t)
-          tma_load_4d(base + t * kWgTileBytes, &tmap_x, 0, j0 + t % 3 - 1, i + t / 3 - 1, n,
-                      full + stage);
-        tma_load_4d(base + 10 * kWgTileBytes, &tmap_dy, 0, j0, i, n, full + stage);
+        mbar_expect_tx(full + stage, kWgStageTx);
+        for (int a = 0; a < 3; ++a)
+          tma_load_4d(base + a * kWgSlot, &tmap_x, 0, j0 - 1, i + a - 1, n, full + stage);
+        tma_load_4d(base + kWgDyOff, &tmap_dy, 0, j0 - 2, i, n, full + stage);
         if (++stage == kWgStages) {
           stage = 0;
           phase ^= 1;
@@ -526,14 +538,15 @@ __global__ void __launch_bounds__(kDenseThreads, 1)
         }
         tc_fence_after();
         const uint32_t base = s_addr(smem + stage * kWgStageBytes);
-        const uint32_t dy_base = base + 10 * kWgTileBytes;
+        const uint32_t dy_base = base + kWgDyOff;  // N block s' = 0, 1, 2 -> shift s = 2, 1, 0
 #pragma unroll
-        for (int q = 0; q < kWgPairs; ++q) {
+        for (int g = 0; g < 2; ++g) {
+          const uint32_t a0 = base + g * 2 * kWgSlot;
+          const uint32_t lbo = g == 0 ? kWgSlot : 128;
 #pragma unroll
           for (int k = 0; k < kWgTileP / 16; ++k) {
-            tc_mma(tmem_base + (uint32_t)(q * 64),
-                   sw128_desc_mn(base + 2 * q * kWgTileBytes + k * 2048, kWgTileBytes),
-                   sw128_desc_mn(dy_base + k * 2048, kWgTileBytes), kDenseIdescMN,
+            tc_mma(tmem_base + (uint32_t)(g * 256), sw128_desc_mn(a0 + k * 2048, lbo),
+                   sw128_desc_mn(dy_base + k * 2048, 128), kWgIdesc,
                    (first && k == 0) ? 0u : 1u);
           }
         }
@@ -548,27 +561,37 @@ __global__ void __launch_bounds__(kDenseThreads, 1)
       else mbar_arrive(done);
     }
   } else {
-    // epilogue: TMEM -> FP32 partials of this CTA
+    // epilogue: TMEM -> FP32 partials [tap][c][o] of this CTA.  TMEM lane
+    // (row) = (half, c); MMA g, half h holds filter row a = 2g + h; column
+    // block s' holds tap column b = 2 - s'.
     const int quad = warp & 3;
-    const int row = quad * 32 + lane;
+    const int half = quad >> 1, c = (quad & 1) * 32 + lane;
     const bool any = (int64_t)blockIdx.x < p.num_tiles;
     if (any && mbar_wait(done, 0) && !s_abort) {
       tc_fence_after();
       float* out = p.partials + (int64_t)blockIdx.x * kWgPartialFloats;
-      for (int q = 0; q < kWgPairs; ++q) {
-        float v[64];
+      for (int g = 0; g < 2; ++g) {
+        const int a = 2 * g + half;
+        for (int sb = 0; sb < 3; ++sb) {
+          float v[64];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          float part[16];
-          tc_ld16(tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(q * 64 + 16 * c), part);
+          for (int q = 0; q < 4; ++q) {
+            float part[16];
+            tc_ld16(tmem_base + ((uint32_t)(quad * 32) << 16) +
+                        (uint32_t)(g * 256 + sb * 64 + 16 * q),
+                    part);
 #pragma unroll
-          for (int z = 0; z < 16; ++z) v[16 * c + z] = part[z];
+            for (int z = 0; z < 16; ++z) v[16 * q + z] = part[z];
+          }
+          tc_wait_ld();
+          if (a < 3) {  // a == 3: the discarded half of MMA 1
+            const int tap = 3 * a + (2 - sb);
+            float4* dst = reinterpret_cast<float4*>(out + ((int64_t)tap * kDenseC + c) * kDenseC);
+#pragma unroll
+            for (int z = 0; z < 16; ++z)
+              dst[z] = make_float4(v[4 * z], v[4 * z + 1], v[4 * z + 2], v[4 * z + 3]);
+          }
         }
-        tc_wait_ld();
-        float4* dst = reinterpret_cast<float4*>(out + ((int64_t)q * 128 + row) * kDenseC);
-#pragma unroll
-        for (int z = 0; z < 16; ++z)
-          dst[z] = make_float4(v[4 * z], v[4 * z + 1], v[4 * z + 2], v[4 * z + 3]);
       }
     } else if (any) {
       dense_fail(p.err, &s_abort);
@@ -585,8 +608,7 @@ __global__ void __launch_bounds__(kDenseThreads, 1)
   }
 }
 
-// dw[o][a][b][c] = sum over CTAs (in order, FP64) of partial[cta][q][row][o]
-// with tap = 2q + row / 64, c = row % 64.
+// dw[o][a][b][c] = sum over CTAs (in order, FP64) of partial[cta][3a + b][c][o].
 __global__ void dense_wgrad_finalize_kernel(const float* __restrict__ partials, int ctas,
                                             float* __restrict__ dw) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
@@ -594,10 +616,9 @@ __global__ void dense_wgrad_finalize_kernel(const float* __restrict__ partials, 
   const int c = idx % kDenseC;
   const int tap = (idx / kDenseC) % kDenseTaps;
   const int o = idx / (kDenseC * kDenseTaps);
-  const int q = tap / 2, row = (tap % 2) * 64 + c;
   double s = 0.0;
   for (int b = 0; b < ctas; ++b)
-    s += (double)partials[(int64_t)b * kWgPartialFloats + ((int64_t)q * 128 + row) * kDenseC + o];
+    s += (double)partials[(int64_t)b * kWgPartialFloats + ((int64_t)tap * kDenseC + c) * kDenseC + o];
   dw[idx] = (float)s;
 }
 
@@ -656,8 +677,8 @@ cudaError_t dense_wgrad_launch(const void* x, const void* dy, float* dw, int64_t
   EncodeFn enc = encode_fn();
   if (!enc) return cudaErrorNotSupported;
   CUtensorMap tx, tdy;
-  if (!make_nhwc_map(enc, &tx, x, N, H, W, kWgTileP) ||
-      !make_nhwc_map(enc, &tdy, dy, N, H, W, kWgTileP))
+  if (!make_nhwc_map(enc, &tx, x, N, H, W, kWgXPx) ||
+      !make_nhwc_map(enc, &tdy, dy, N, H, W, kWgDyPx))
     return cudaErrorInvalidValue;
   int* err = nullptr;
   cudaError_t e = cudaGetSymbolAddress(reinterpret_cast<void**>(&err), g_dense_err);
@@ -670,7 +691,7 @@ cudaError_t dense_wgrad_launch(const void* x, const void* dy, float* dw, int64_t
   prm.N = (int)N;
   prm.H = (int)H;
   prm.W = (int)W;
-  prm.tiles_w = (int)((W + kWgTileP - 1) / kWgTileP);
+  prm.tiles_w = (int)((W + 2 + kWgTileP - 1) / kWgTileP);  // every pixel once for each shift
   prm.num_tiles = N * H * prm.tiles_w;
   const int grid = (int)std::min<int64_t>(std::min<int64_t>(prm.num_tiles, device_sms()),
                                           kWgMaxCtas);

@@ -42,7 +42,8 @@ def test_dense_fwd_and_input_grad(giga, shape):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("shape", [(1, 1, 1), (2, 5, 200), (1, 3, 300), (3, 17, 64)])
+@pytest.mark.parametrize("shape", [(1, 1, 1), (2, 5, 200), (1, 3, 300), (3, 17, 64),
+                                   (1, 4, 62), (1, 4, 63), (2, 3, 128), (1, 2, 191)])
 def test_dense_filter_grad(giga, shape):
     """dw[o][a][b][c] = sum_{n,i,j} dy[n,i,j,o] x~[n,i+a-1,j+b-1,c] on the tensor
     cores (FP32 accumulation), FP64 across CTAs.  Bound: the FP32 accumulation
@@ -78,6 +79,34 @@ def test_dense_full_size_sampled(giga):
     ref = oracle.dense_fwd_points(x.double().numpy(), w.double().numpy(), oracle.ZERO,
                                   idx.numpy())
     assert normwise(got, ref) <= BF16_KERNEL_TOL
+
+
+@pytest.mark.gpu
+def test_dense_filter_grad_full_size_banded_dy(giga):
+    """The filter gradient on the 8 x 1024 x 1024 x 64 workload in the launch
+    configuration the benchmark uses, with dy zero outside two 8-row bands (in
+    images 2 and 7): dw then equals the oracle's filter gradient of the
+    10-row crops around the bands (the zero rows at the crop ends stand for the
+    zero dy outside), so every CTA, chunk and the FP64 cross-CTA sum run at
+    full size while the oracle works on 2 x 10 x 1024 pixels."""
+    x, _, dy = workloads.dense()
+    mask = torch.zeros((8, 1024, 1, 1), dtype=torch.bool)
+    mask[2, 300:308] = True
+    mask[7, 1016:1024] = True
+    dyb = torch.where(mask, dy, torch.zeros_like(dy))
+    dw = giga.dense_conv2d_bwd_filter(x.cuda(), dyb.cuda(),
+                                      out=torch.full((64, 3, 3, 64), float("nan"), device="cuda"))
+    giga.check_device_error()
+    xs = torch.cat([x[2:3, 299:309], torch.cat([x[7:8, 1015:1024],
+                                                torch.zeros_like(x[7:8, :1])], 1)]).double()
+    dys = torch.cat([dyb[2:3, 299:309], torch.cat([dyb[7:8, 1015:1024],
+                                                   torch.zeros_like(dyb[7:8, :1])], 1)]).double()
+    ref = oracle.dense_bwd_filter(xs.numpy(), dys.numpy(), 3, oracle.ZERO)
+    mag = oracle.dense_bwd_filter(np.abs(xs.numpy()), np.abs(dys.numpy()), 3, oracle.ZERO)
+    got = to_np(dw)
+    assert not np.isnan(got).any()
+    assert (np.abs(got - ref) <= 2 * gamma(8 * 1024 * 1024) * mag + 1e-30).all()
+    assert normwise(got, ref) <= FP32_TOL
 
 
 def test_dense_rejects_unsupported():
