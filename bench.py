@@ -360,6 +360,7 @@ def compare_ragged(dev, iters):
     stream = torch.cuda.current_stream(dev)
     plan = giga.BatchedPlan(imgs, 7, "zero")
     plan.upload()
+    tpc = plan.autotune()   # tiles per chunk of the persistent launch, before capture
     torch.cuda.synchronize(dev)
     s = torch.cuda.Stream(dev)
     s.wait_stream(stream)
@@ -391,7 +392,8 @@ def compare_ragged(dev, iters):
     px = sum(3 * h * w_ for h, w_, _ in shapes)
     return {"workload": f"{len(shapes)} images 3 x U[64,4096]^2, K in {{3,5,9,11}}, zero border, "
                         "fwd+bwd",
-            "pixels": px, "graph_persistent": {"ms": ms_graph, "value": taps / (ms_graph * 1e-3) / 1e9},
+            "pixels": px, "graph_persistent": {"ms": ms_graph, "value": taps / (ms_graph * 1e-3) / 1e9,
+                                               "tiles_per_chunk_autotuned": tpc},
             "per_image_loop": {"ms": ms_loop, "value": taps / (ms_loop * 1e-3) / 1e9,
                                "launches": 4 * len(imgs)},
             "speedup": ms_loop / ms_graph,

@@ -165,6 +165,20 @@ giga_status_t giga_batched_plan_upload(giga_batched_plan_t plan, void* ws, size_
 giga_status_t giga_batched_plan_run(giga_batched_plan_t plan, void* ws, size_t ws_bytes,
                                     void* stream);
 void giga_batched_plan_destroy(giga_batched_plan_t plan);
+/* Autotuner of the ragged launch (the paper has no tuner): times the
+ * persistent launch with 1, 2, 4, 8, 16 and 32 tiles per chunk (a chunk is the
+ * unit a CTA takes from the work counter; smaller chunks balance the tail,
+ * larger ones cut the per-chunk reduction) on the caller's buffers -- the
+ * outputs are overwritten -- then rebuilds and uploads the table for the
+ * fastest.  Synchronises `stream`; not capturable
+ * (GIGA_ERR_INVALID_ARG while the stream is capturing): call it before
+ * capturing giga_batched_plan_run.  The plan's workspace size already covers
+ * every candidate.  *tiles_per_chunk (may be NULL) receives the choice; the
+ * default before any tuning is 4. */
+giga_status_t giga_batched_plan_autotune(giga_batched_plan_t plan, void* ws, size_t ws_bytes,
+                                         void* stream, int32_t* tiles_per_chunk);
+/* Tiles per chunk the plan currently uses; -1 for a NULL plan. */
+int32_t giga_batched_plan_tiles_per_chunk(giga_batched_plan_t plan);
 
 /* Convenience: create + upload + run + destroy (blocks until the table copy
  * has left host memory; not capturable). */

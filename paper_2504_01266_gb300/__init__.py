@@ -272,6 +272,16 @@ class BatchedPlan:
                                               _stream(self.device)),
                    "giga_batched_plan_run")
 
+    def autotune(self) -> int:
+        """Time the launch at 1 to 32 tiles per chunk (powers of 2) on these buffers
+        (outputs overwritten), keep the fastest; returns it.  Not capturable."""
+        return _lib.giga_batched_plan_autotune(self.plan, self.ws.data_ptr(), self.ws.numel(),
+                                               _stream(self.device))
+
+    @property
+    def tiles_per_chunk(self) -> int:
+        return _lib.giga_batched_plan_tiles_per_chunk(self.plan)
+
     def close(self):
         if self.plan:
             _lib.giga_batched_plan_destroy(self.plan)

@@ -42,6 +42,7 @@ EXPORTS = (
     "giga_batched_plan_create",
     "giga_batched_plan_workspace_size", "giga_batched_plan_upload", "giga_batched_plan_run",
     "giga_batched_plan_destroy", "giga_conv2d_batched", "giga_conv2d_batched_workspace_size",
+    "giga_batched_plan_autotune", "giga_batched_plan_tiles_per_chunk",
     "giga_upsample_batched_plan_create", "giga_upsample_batched_plan_workspace_size",
     "giga_upsample_batched_plan_upload", "giga_upsample_batched_plan_run",
     "giga_upsample_batched_plan_destroy", "giga_upsample_conv2d_batched",
@@ -111,6 +112,8 @@ _SIGS = {
     "giga_batched_plan_upload": (_ST, [_P, _P, _SZ, _P]),
     "giga_batched_plan_run": (_ST, [_P, _P, _SZ, _P]),
     "giga_batched_plan_destroy": (None, [_P]),
+    "giga_batched_plan_autotune": (_ST, [_P, _P, _SZ, _P, ctypes.POINTER(_I32)]),
+    "giga_batched_plan_tiles_per_chunk": (_I32, [_P]),
     "giga_conv2d_batched": (_ST, [_IMG, _I32, _I32, _I32, _I32, _P, _SZ, _P]),
     "giga_conv2d_batched_workspace_size": (_ST, [_IMG, _I32, _I32, ctypes.POINTER(_SZ)]),
     "giga_upsample_batched_plan_create": (_ST, [_UPIMG, _I32, _I32, _I32, ctypes.POINTER(_P)]),
@@ -248,6 +251,18 @@ def giga_batched_plan_run(plan, ws, ws_bytes, stream) -> int:
 
 def giga_batched_plan_destroy(plan) -> None:
     load().giga_batched_plan_destroy(plan)
+
+
+def giga_batched_plan_autotune(plan, ws, ws_bytes, stream) -> int:
+    """Returns the chosen tiles per chunk (raises on error)."""
+    tpc = _I32(0)
+    check(load().giga_batched_plan_autotune(plan, ws, ws_bytes, stream, ctypes.byref(tpc)),
+          "giga_batched_plan_autotune")
+    return int(tpc.value)
+
+
+def giga_batched_plan_tiles_per_chunk(plan) -> int:
+    return int(load().giga_batched_plan_tiles_per_chunk(plan))
 
 
 def giga_conv2d_batched(images, n, ops, border, dtype, ws, ws_bytes, stream) -> int:

@@ -15,16 +15,19 @@
 using namespace giga;
 
 struct giga_batched_plan_s {
+  std::vector<giga_image_t> descs;  // the caller's descriptors (rebuilt per chunk size)
   std::vector<RagImage> images;
   std::vector<RagChunk> chunks;
+  int tpc = kRagTilesPerChunk;      // tiles per chunk
   std::vector<int> empty_filter_grads;  // images whose dw must be zeroed (no pixels)
   int ops = 0, border = 0, dtype = 0;
   int n_ic = 0;
   int max_k = 1;
   int64_t partial_floats = 0;
   size_t off_chunks = 0, off_counters = 0, off_partials = 0, ws_bytes = 0;
+  size_t ws_max = 0, table_max = 0;  // over every tiles-per-chunk candidate (the smallest chunks)
   void* pinned = nullptr;
-  size_t table_bytes = 0;
+  size_t table_bytes = 0, pinned_bytes = 0;
   cudaEvent_t uploaded = nullptr;
   bool pending = false;
 };
@@ -80,7 +83,7 @@ int vec_image(const giga_image_t& im, int dtype) {
 
 // Builds everything but device state.  check_ptrs = false for size queries.
 giga_status_t build_plan(const giga_image_t* images, int32_t n, int32_t ops, int32_t border,
-                         int32_t dtype, bool check_ptrs, giga_batched_plan_s* plan) {
+                         int32_t dtype, bool check_ptrs, int tpc, giga_batched_plan_s* plan) {
   if (n < 0 || (n > 0 && !images)) return fail(GIGA_ERR_INVALID_ARG, "bad image list");
   if (ops <= 0 || (ops & ~(GIGA_OP_FWD | GIGA_OP_BWD_INPUT | GIGA_OP_BWD_FILTER)))
     return fail(GIGA_ERR_INVALID_ARG, "ops must be a non-empty GIGA_OP_* bitmask");
@@ -90,7 +93,11 @@ giga_status_t build_plan(const giga_image_t* images, int32_t n, int32_t ops, int
   plan->ops = ops;
   plan->border = border;
   plan->dtype = dtype;
+  plan->tpc = tpc;
   plan->images.resize(n);
+  plan->chunks.clear();
+  plan->empty_filter_grads.clear();
+  plan->max_k = 1;
   std::vector<int64_t> tiles(n, 0);
   int64_t ic = 0, pf = 0, n_chunks = 0;
   for (int i = 0; i < n; ++i) {
@@ -112,7 +119,7 @@ giga_status_t build_plan(const giga_image_t* images, int32_t n, int32_t ops, int
       continue;
     }
     tiles[i] = ((g.W + kTileW - 1) / kTileW) * (int64_t)((g.H + kBwdTileH - 1) / kBwdTileH);
-    r.nch = (int)((tiles[i] + kRagTilesPerChunk - 1) / kRagTilesPerChunk);
+    r.nch = (int)((tiles[i] + tpc - 1) / tpc);
     r.ic_base = (int)ic;
     r.partial_base = pf;
     ic += g.C;
@@ -137,8 +144,8 @@ giga_status_t build_plan(const giga_image_t* images, int32_t n, int32_t ops, int
     if (tiles[i] == 0) continue;
     for (int c = 0; c < r.C; ++c)
       for (int j = 0; j < r.nch; ++j) {
-        const int t0 = j * kRagTilesPerChunk;
-        plan->chunks.push_back({i, c, t0, (int)std::min<int64_t>(t0 + kRagTilesPerChunk, tiles[i])});
+        const int t0 = j * tpc;
+        plan->chunks.push_back({i, c, t0, (int)std::min<int64_t>(t0 + tpc, tiles[i])});
       }
   }
   plan->n_ic = (int)ic;
@@ -153,10 +160,28 @@ giga_status_t build_plan(const giga_image_t* images, int32_t n, int32_t ops, int
 
 giga_status_t check_plan_ws(const giga_batched_plan_s* plan, void* ws, size_t ws_bytes) {
   if (!ws) return fail(GIGA_ERR_WORKSPACE, "workspace is NULL");
-  if (ws_bytes < plan->ws_bytes)
-    return fail(GIGA_ERR_WORKSPACE, "workspace too small, need " + std::to_string(plan->ws_bytes));
+  if (ws_bytes < plan->ws_max)
+    return fail(GIGA_ERR_WORKSPACE, "workspace too small, need " + std::to_string(plan->ws_max));
   if (reinterpret_cast<uintptr_t>(ws) % 256)
     return fail(GIGA_ERR_WORKSPACE, "workspace must be 256-byte aligned");
+  return GIGA_OK;
+}
+
+// Tiles per chunk the plan can use; the autotuner times each of them.
+constexpr int kRagTpcCandidates[] = {1, 2, 4, 8, 16, 32};
+
+// Build the plan for tiles-per-chunk `tpc`, with workspace and table sizes
+// that fit every candidate (the smallest chunks need the most of both).
+giga_status_t build_plan_sized(const giga_image_t* images, int32_t n, int32_t ops,
+                               int32_t border, int32_t dtype, bool check_ptrs, int tpc,
+                               giga_batched_plan_s* plan) {
+  giga_status_t s = build_plan(images, n, ops, border, dtype, check_ptrs, 1, plan);
+  if (s != GIGA_OK) return s;
+  const size_t ws_max = plan->ws_bytes, table_max = plan->table_bytes;
+  if (tpc != 1 && (s = build_plan(images, n, ops, border, dtype, false, tpc, plan)) != GIGA_OK)
+    return s;
+  plan->ws_max = ws_max;
+  plan->table_max = table_max;
   return GIGA_OK;
 }
 
@@ -172,11 +197,13 @@ giga_status_t giga_batched_plan_create(const giga_image_t* images, int32_t n, in
   *plan = nullptr;
   auto* p = new (std::nothrow) giga_batched_plan_s();
   if (!p) return fail(GIGA_ERR_INVALID_ARG, "out of host memory");
-  giga_status_t s = build_plan(images, n, ops, border, dtype, true, p);
+  giga_status_t s =
+      build_plan_sized(images, n, ops, border, dtype, true, kRagTilesPerChunk, p);
   if (s != GIGA_OK) {
     delete p;
     return s;
   }
+  if (n > 0) p->descs.assign(images, images + n);
   *plan = p;
   return GIGA_OK;
 }
@@ -184,7 +211,7 @@ giga_status_t giga_batched_plan_create(const giga_image_t* images, int32_t n, in
 giga_status_t giga_batched_plan_workspace_size(giga_batched_plan_t plan, size_t* bytes) {
   clear_error();
   if (!plan || !bytes) return fail(GIGA_ERR_INVALID_ARG, "NULL argument");
-  *bytes = plan->ws_bytes;
+  *bytes = plan->ws_max;
   return GIGA_OK;
 }
 
@@ -201,13 +228,15 @@ giga_status_t giga_batched_plan_upload(giga_batched_plan_t plan, void* ws, size_
     plan->pending = false;
   }
   if (!plan->pinned) {
-    if ((e = cudaMallocHost(&plan->pinned, plan->table_bytes)) != cudaSuccess)
+    if ((e = cudaMallocHost(&plan->pinned, plan->table_max)) != cudaSuccess)
       return cuda_fail(e, "pinned table");
-    std::memset(plan->pinned, 0, plan->table_bytes);
-    std::memcpy(plan->pinned, plan->images.data(), sizeof(RagImage) * plan->images.size());
-    std::memcpy(static_cast<char*>(plan->pinned) + plan->off_chunks, plan->chunks.data(),
-                sizeof(RagChunk) * plan->chunks.size());
+    plan->pinned_bytes = plan->table_max;
   }
+  // the table of the current chunk size (the autotuner rebuilds it)
+  std::memset(plan->pinned, 0, plan->table_bytes);
+  std::memcpy(plan->pinned, plan->images.data(), sizeof(RagImage) * plan->images.size());
+  std::memcpy(static_cast<char*>(plan->pinned) + plan->off_chunks, plan->chunks.data(),
+              sizeof(RagChunk) * plan->chunks.size());
   if (!plan->uploaded && (e = cudaEventCreateWithFlags(&plan->uploaded, cudaEventDisableTiming)))
     return cuda_fail(e, "event");
   if ((e = cudaMemcpyAsync(ws, plan->pinned, plan->table_bytes, cudaMemcpyHostToDevice, st)))
@@ -241,6 +270,7 @@ giga_status_t giga_batched_plan_run(giga_batched_plan_t plan, void* ws, size_t w
   p.counters = reinterpret_cast<int*>(base + plan->off_counters);
   p.partials = reinterpret_cast<float*>(base + plan->off_partials);
   p.n_chunks = (int)plan->chunks.size();
+  p.tpc = plan->tpc;
   p.ops = plan->ops;
   p.border = plan->border;
   if (plan->max_k > kRagMaxK) return fail(GIGA_ERR_INVALID_ARG, "filter size above the batched limit");
@@ -283,10 +313,65 @@ giga_status_t giga_conv2d_batched_workspace_size(const giga_image_t* images, int
   if (!bytes) return fail(GIGA_ERR_INVALID_ARG, "bytes is NULL");
   *bytes = 0;
   giga_batched_plan_s plan;
-  giga_status_t s = build_plan(images, n, ops, GIGA_BORDER_ZERO, GIGA_F32, false, &plan);
+  giga_status_t s =
+      build_plan_sized(images, n, ops, GIGA_BORDER_ZERO, GIGA_F32, false, kRagTilesPerChunk, &plan);
   if (s != GIGA_OK) return s;
-  *bytes = plan.ws_bytes;
+  *bytes = plan.ws_max;
   return GIGA_OK;
+}
+
+giga_status_t giga_batched_plan_autotune(giga_batched_plan_t plan, void* ws, size_t ws_bytes,
+                                         void* stream, int32_t* tiles_per_chunk) {
+  clear_error();
+  if (!plan) return fail(GIGA_ERR_INVALID_ARG, "plan is NULL");
+  giga_status_t s = check_plan_ws(plan, ws, ws_bytes);
+  if (s != GIGA_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if ((e = cudaStreamIsCapturing(st, &cap)) != cudaSuccess) return cuda_fail(e, "capture query");
+  if (cap != cudaStreamCaptureStatusNone)
+    return fail(GIGA_ERR_INVALID_ARG, "the autotuner cannot run while the stream is capturing");
+  const int n = (int)plan->descs.size();
+  const giga_image_t* im = n ? plan->descs.data() : nullptr;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  for (auto& x : ev)
+    if ((e = cudaEventCreate(&x)) != cudaSuccess) return cuda_fail(e, "event");
+  float best_ms = 0.f;
+  int best = plan->tpc;
+  for (int tpc : kRagTpcCandidates) {
+    if ((s = build_plan(im, n, plan->ops, plan->border, plan->dtype, false, tpc, plan)) != GIGA_OK)
+      break;
+    if ((s = giga_batched_plan_upload(plan, ws, ws_bytes, stream)) != GIGA_OK) break;
+    if ((s = giga_batched_plan_run(plan, ws, ws_bytes, stream)) != GIGA_OK) break;  // warm-up
+    float ms = 0.f;
+    cudaEventRecord(ev[0], st);
+    for (int r = 0; r < 3 && s == GIGA_OK; ++r) s = giga_batched_plan_run(plan, ws, ws_bytes, stream);
+    if (s != GIGA_OK) break;
+    cudaEventRecord(ev[1], st);
+    if ((e = cudaEventSynchronize(ev[1])) != cudaSuccess ||
+        (e = cudaEventElapsedTime(&ms, ev[0], ev[1])) != cudaSuccess) {
+      s = cuda_fail(e, "autotune timing");
+      break;
+    }
+    if (tpc == kRagTpcCandidates[0] || ms < best_ms) {
+      best_ms = ms;
+      best = tpc;
+    }
+  }
+  for (auto& x : ev) cudaEventDestroy(x);
+  if (s != GIGA_OK) return s;
+  // rebuild and upload the chosen table
+  if ((s = build_plan(im, n, plan->ops, plan->border, plan->dtype, false, best, plan)) != GIGA_OK)
+    return s;
+  if ((s = giga_batched_plan_upload(plan, ws, ws_bytes, stream)) != GIGA_OK) return s;
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "autotune sync");
+  if (tiles_per_chunk) *tiles_per_chunk = best;
+  return GIGA_OK;
+}
+
+int32_t giga_batched_plan_tiles_per_chunk(giga_batched_plan_t plan) {
+  return plan ? plan->tpc : -1;
 }
 
 }  // extern "C"

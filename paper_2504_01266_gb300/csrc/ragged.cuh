@@ -4,7 +4,8 @@
 // The GigaAPI paper wanted to process a "database" of images in one go and
 // gave up (Section 5, "No Batch Processing for Images"); this kernel does it:
 //  * the host cuts every (image, channel) into chunks of up to 4 tiles of
-//    64 x 128 pixels and sorts the chunks longest first (cost K^2 per pixel);
+//    64 x 128 pixels (1 to 32, powers of 2: the plan's autotuner times them) and
+//    sorts the chunks longest first (cost K^2 per pixel);
 //  * CTAs (one per SM, 12 warps) pull chunk numbers from an atomic counter,
 //    stage each tile's x and dy once, and run the three ops on it with fixed
 //    warp roles: warps 0-3 forward, 4-7 input gradient, 8-11 filter gradient;
@@ -21,7 +22,7 @@
 namespace giga {
 
 constexpr int kRagThreads = 384;
-constexpr int kRagTilesPerChunk = 4;
+constexpr int kRagTilesPerChunk = 4;  // the plan's default; the autotuner may pick 1 to 32
 constexpr int kRagMaxK = 15;
 
 struct RagImage {
@@ -49,6 +50,7 @@ struct RagParams {
   int* counters;  // [0]: work counter, [1 + ic]: finished chunks of (image, channel) ic
   float* partials;
   int n_chunks;
+  int tpc;  // tiles per chunk
   int ops;  // GIGA_OP_* bitmask
   int border;
 };
@@ -211,7 +213,7 @@ __device__ __forceinline__ int rag_chunk(const RagParams& p, const RagChunk& ch,
   const int ic = im.ic_base + ch.channel;
   float* part_c = p.partials + im.partial_base + (int64_t)ch.channel * im.nch * KK;
   if (do_dw) {
-    const int j = ch.tile_begin / kRagTilesPerChunk;
+    const int j = ch.tile_begin / p.tpc;
     for (int k = threadIdx.x; k < KK; k += kRagThreads) {
       const int a = k / K, b = k - (k / K) * K;
       int gg = 0;

@@ -118,6 +118,46 @@ def test_ragged_bf16(giga):
     plan.close()
 
 
+@pytest.mark.gpu
+def test_ragged_autotune_chunk_sizes(giga):
+    """The plan's autotuner times 1 to 32 tiles per chunk (powers of 2), keeps one;
+    every chunk size gives the same y and dx bit for bit (per-pixel arithmetic
+    does not depend on the chunking) and a filter gradient within the FP32
+    bound; the tuned plan captures and replays in a CUDA graph; the tuner
+    refuses to run while the stream is capturing."""
+    imgs = workloads.ragged(n=10, lo=40, hi=600, ks=(3, 5, 9, 11))
+    b = batch(imgs)
+    plan = giga.BatchedPlan(b, ALL, "zero")
+    assert plan.tiles_per_chunk == 4
+    plan.upload()
+    plan.run()
+    torch.cuda.synchronize()
+    ref = [(t["y"].clone(), t["dx"].clone(), t["dw"].clone()) for t in b]
+    tpc = plan.autotune()
+    assert tpc in (1, 2, 4, 8, 16, 32) and plan.tiles_per_chunk == tpc
+    for t in b:
+        for k in ("y", "dx", "dw"):
+            t[k].fill_(float("nan"))
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(graph, stream=s):
+            plan.run()
+            from paper_2504_01266_gb300 import _lib
+            with pytest.raises(_lib.GigaError):
+                plan.autotune()
+    graph.replay()
+    torch.cuda.synchronize()
+    for im, t, (y, dx, dw) in zip(imgs, b, ref):
+        assert torch.equal(t["y"], y) and torch.equal(t["dx"], dx)
+        x, dyn = im.x.numpy(), im.dy.numpy()
+        assert_fp32(to_np(t["dw"]), oracle.dw_bwd_filter(x, dyn, im.K, 0),
+                    oracle.dw_bwd_filter(np.abs(x), np.abs(dyn), im.K, 0), im.H * im.W,
+                    ("dw", im.H, im.W, im.K, tpc))
+    plan.close()
+
+
 # ------------------------------------------------------- host-side checks
 
 def _img(lib, H=10, W=10, C=1, K=3, p=0x100000):
