@@ -28,11 +28,11 @@ sys.path.insert(0, ROOT)
 N, C, H, W = 8, 3, 4096, 4096
 KS = (3, 7, 15)
 # DRAM bytes (read + written) per pixel of one launch, from the ncu capture of
-# one 1x3x4096x4096 launch of the kernel (dram__bytes_read.sum 201.376 MB +
-# dram__bytes_write.sum 154.844 MB); traffic grows with the pixel count, so a
+# one 1x3x4096x4096 launch of the kernel (dram__bytes_read.sum 201.377 MB +
+# dram__bytes_write.sum 154.670 MB); traffic grows with the pixel count, so a
 # launch over 8 such images moves 8x that.
 NCU_DRAM_BYTES_PER_PX = {
-    "dw_fwd_kernel<float,15,8>": (201376000 + 154843904) / (3 * 4096 * 4096),
+    "dw_fwd_kernel<float,15,8>": (201376512 + 154669824) / (3 * 4096 * 4096),
 }
 METRIC = "Gpixel*tap/s fwd+bwd (depthwise KxK, K in {3,7,15})"
 UNIT = "Gpixel*tap/s"
