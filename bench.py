@@ -6,8 +6,9 @@ upstream gradient normal(0, 1).  One step = for every K: the forward filter
 and the fused backward pass (input gradient + filter gradient), all through
 the C ABI.  Metric: Gpixel*tap/s = sum_K 3 * N*C*H*W*K^2 / step time.
 
-Prints ONE JSON line.  `--impl reference` times the FP64 CPU oracle (the
-reference arm of this build) on a bounded sample of the same workload.
+Prints ONE JSON line.  `--impl reference` times the FP64 CPU oracle (there
+is no other reference implementation of this path) on a bounded sample of
+the same workload.
 Multi-GPU (torchrun): independent replicas, one per GPU, no collective on the
 data path; value = work of all ranks / max-over-ranks time.
 """
