@@ -161,7 +161,10 @@ giga_status_t giga_batched_plan_workspace_size(giga_batched_plan_t plan, size_t*
 giga_status_t giga_batched_plan_upload(giga_batched_plan_t plan, void* ws, size_t ws_bytes,
                                        void* stream);
 /* One persistent launch for all images (plus a memset of its counters).
- * Capturable into a CUDA graph once the table has been uploaded. */
+ * Capturable into a CUDA graph once the table has been uploaded.  `ws` must be
+ * the workspace the current table was uploaded to (GIGA_ERR_WORKSPACE
+ * otherwise); after a failed giga_batched_plan_autotune the plan refuses to
+ * run (GIGA_ERR_INVALID_ARG) until it is uploaded again. */
 giga_status_t giga_batched_plan_run(giga_batched_plan_t plan, void* ws, size_t ws_bytes,
                                     void* stream);
 void giga_batched_plan_destroy(giga_batched_plan_t plan);
@@ -261,7 +264,8 @@ giga_status_t giga_upsample_batched_plan_workspace_size(giga_upsample_batched_pl
 giga_status_t giga_upsample_batched_plan_upload(giga_upsample_batched_plan_t plan, void* ws,
                                                 size_t ws_bytes, void* stream);
 /* One launch per filter size present in the batch.  Capturable into a CUDA
- * graph once the table has been uploaded. */
+ * graph once the table has been uploaded; `ws` must be the workspace it was
+ * uploaded to (GIGA_ERR_WORKSPACE otherwise). */
 giga_status_t giga_upsample_batched_plan_run(giga_upsample_batched_plan_t plan, void* ws,
                                              size_t ws_bytes, void* stream);
 void giga_upsample_batched_plan_destroy(giga_upsample_batched_plan_t plan);

@@ -19,6 +19,8 @@ struct giga_batched_plan_s {
   std::vector<RagImage> images;
   std::vector<RagChunk> chunks;
   int tpc = kRagTilesPerChunk;      // tiles per chunk
+  int uploaded_tpc = 0;             // tiles per chunk of the table last uploaded (0: none)
+  const void* uploaded_ws = nullptr;  // the workspace that table went to
   std::vector<int> empty_filter_grads;  // images whose dw must be zeroed (no pixels)
   int ops = 0, border = 0, dtype = 0;
   int n_ic = 0;
@@ -243,6 +245,8 @@ giga_status_t giga_batched_plan_upload(giga_batched_plan_t plan, void* ws, size_
     return cuda_fail(e, "table upload");
   if ((e = cudaEventRecord(plan->uploaded, st))) return cuda_fail(e, "event record");
   plan->pending = true;
+  plan->uploaded_tpc = plan->tpc;
+  plan->uploaded_ws = ws;
   return GIGA_OK;
 }
 
@@ -253,6 +257,11 @@ giga_status_t giga_batched_plan_run(giga_batched_plan_t plan, void* ws, size_t w
   giga_status_t s = check_plan_ws(plan, ws, ws_bytes);
   if (s != GIGA_OK) return s;
   if (!plan->uploaded) return fail(GIGA_ERR_INVALID_ARG, "plan was never uploaded");
+  // the kernels index the chunk table in the workspace: it must be this plan's
+  if (plan->uploaded_tpc != plan->tpc)
+    return fail(GIGA_ERR_INVALID_ARG, "the plan's table changed since its upload; upload it again");
+  if (ws != plan->uploaded_ws)
+    return fail(GIGA_ERR_WORKSPACE, "run with the workspace the table was uploaded to");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   char* base = static_cast<char*>(ws);
   cudaError_t e;
@@ -338,7 +347,8 @@ giga_status_t giga_batched_plan_autotune(giga_batched_plan_t plan, void* ws, siz
   for (auto& x : ev)
     if ((e = cudaEventCreate(&x)) != cudaSuccess) return cuda_fail(e, "event");
   float best_ms = 0.f;
-  int best = plan->tpc;
+  const int prev = plan->tpc;
+  int best = prev;
   for (int tpc : kRagTpcCandidates) {
     if ((s = build_plan(im, n, plan->ops, plan->border, plan->dtype, false, tpc, plan)) != GIGA_OK)
       break;
@@ -360,7 +370,14 @@ giga_status_t giga_batched_plan_autotune(giga_batched_plan_t plan, void* ws, siz
     }
   }
   for (auto& x : ev) cudaEventDestroy(x);
-  if (s != GIGA_OK) return s;
+  if (s != GIGA_OK) {
+    // leave the plan describing its previous table; run() refuses it until the
+    // caller uploads again, so no launch can read a table of another size
+    const std::string detail = giga_last_error_detail();
+    build_plan(im, n, plan->ops, plan->border, plan->dtype, false, prev, plan);
+    plan->uploaded_tpc = 0;
+    return fail(s, detail);
+  }
   // rebuild and upload the chosen table
   if ((s = build_plan(im, n, plan->ops, plan->border, plan->dtype, false, best, plan)) != GIGA_OK)
     return s;

@@ -115,6 +115,7 @@ struct giga_upsample_batched_plan_s {
   size_t ws_bytes = 0;
   void* pinned = nullptr;
   cudaEvent_t uploaded = nullptr;
+  const void* uploaded_ws = nullptr;  // the workspace the table went to
   bool pending = false;
 };
 
@@ -302,6 +303,7 @@ giga_status_t giga_upsample_batched_plan_upload(giga_upsample_batched_plan_t pla
     return cuda_fail(e, "table upload");
   if ((e = cudaEventRecord(plan->uploaded, st))) return cuda_fail(e, "event record");
   plan->pending = true;
+  plan->uploaded_ws = ws;
   return GIGA_OK;
 }
 
@@ -313,6 +315,8 @@ giga_status_t giga_upsample_batched_plan_run(giga_upsample_batched_plan_t plan, 
   if (s != GIGA_OK) return s;
   if (plan->table.empty()) return GIGA_OK;
   if (!plan->uploaded) return fail(GIGA_ERR_INVALID_ARG, "plan was never uploaded");
+  if (ws != plan->uploaded_ws)
+    return fail(GIGA_ERR_WORKSPACE, "run with the workspace the table was uploaded to");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   UpRagParams p;
   p.images = static_cast<const UpRagImage*>(ws);

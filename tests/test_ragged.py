@@ -158,6 +158,29 @@ def test_ragged_autotune_chunk_sizes(giga):
     plan.close()
 
 
+@pytest.mark.gpu
+def test_run_requires_the_uploaded_workspace(giga):
+    """The kernels index the tile table in the workspace: a run with another
+    workspace than the one the table went to is refused before any launch."""
+    from paper_2504_01266_gb300 import _lib
+    imgs = workloads.ragged(n=3, lo=20, hi=90, ks=(3, 5))
+    b = batch(imgs)
+    plan = giga.BatchedPlan(b, ALL, "zero")
+    with pytest.raises(_lib.GigaError):
+        plan.run()                                   # never uploaded
+    plan.upload()
+    other = torch.empty_like(plan.ws)
+    st = _lib.giga_batched_plan_run(plan.plan, other.data_ptr(), other.numel(),
+                                    torch.cuda.current_stream().cuda_stream)
+    assert st == _lib.GIGA_ERR_WORKSPACE
+    plan.run()
+    torch.cuda.synchronize()
+    for im, t in zip(imgs, b):
+        y = giga.conv2d_fwd(im.x.cuda(), im.w.cuda(), "zero")
+        assert torch.equal(t["y"], y[0])
+    plan.close()
+
+
 # ------------------------------------------------------- host-side checks
 
 def _img(lib, H=10, W=10, C=1, K=3, p=0x100000):

@@ -143,6 +143,26 @@ def test_empty_images_and_empty_batch(giga):
 
 
 @pytest.mark.gpu
+def test_run_requires_the_uploaded_workspace(giga):
+    imgs = small_batch(2, 13)
+    dev = to_device(imgs, torch.float32)
+    plan = giga.UpsampleBatchedPlan(dev, "zero")
+    with pytest.raises(_lib.GigaError):
+        plan.run()                                   # never uploaded
+    plan.upload()
+    other = torch.empty_like(plan.ws)
+    st = _lib.giga_upsample_batched_plan_run(plan.plan, other.data_ptr(), other.numel(),
+                                             torch.cuda.current_stream().cuda_stream)
+    assert st == _lib.GIGA_ERR_WORKSPACE
+    plan.run()
+    torch.cuda.synchronize()
+    for d in dev:
+        single = giga.upsample_conv2d(d["x"][None], d["w"], d["scale"], "zero")[0]
+        assert torch.equal(d["y"], single)
+    plan.close()
+
+
+@pytest.mark.gpu
 def test_database_workload_sampled(giga):
     """The benchmark's database (128 images, sides 64-1024, scales 2-8,
     K in {3, 5, 9, 11}, zero border) in one launch: sampled outputs and every
