@@ -873,8 +873,11 @@ struct BwdShape {
   static constexpr int SM_X = 128;
   static constexpr int SM_DY = SM_X + ST::BYTES;
   static constexpr int SM_W = SM_DY + ST::BYTES;
-  static constexpr int SM_RED = SM_W + G::WPAD * 4;
-  static constexpr int SM_BYTES = SM_RED + NDW * AT * K * 4;
+  // the warps' filter-gradient sums are written after every warp has left the
+  // tile loop, so they reuse the x tile's space (3 CTAs per SM fit at K = 7)
+  static constexpr int SM_RED = SM_X;
+  static constexpr int SM_BYTES = SM_W + G::WPAD * 4;
+  static_assert(NDW * AT * K * 4 <= ST::BYTES, "reduction rows fit the x tile");
   static_assert(NDW % GT == 0, "filter-row groups must divide the dw warps");
   static_assert(kBwdTileH % (WPG * 8) == 0, "dw warps own whole 8-row blocks");
   static_assert(16 % bwd_block_rows<K>() == 0, "input-gradient warps own 16 rows");
@@ -886,7 +889,7 @@ __device__ __forceinline__ int group_lo(int g, int K, int GT) { return g * K / G
 // memory-bound and need fewer registers, so a third CTA adds loads in flight.
 template <typename T, int K>
 constexpr int bwd_min_ctas() {
-  return K <= 5 ? 3 : 2;
+  return (K <= 5 || (K == 7 && sizeof(T) == 4)) ? 3 : 2;
 }
 
 template <typename T, int K>
