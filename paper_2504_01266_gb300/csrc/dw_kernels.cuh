@@ -623,8 +623,8 @@ struct FwdShape {
 };
 
 template <typename T, int K, int PY>
-__global__ void __launch_bounds__(kThreads) dw_fwd_kernel(
-    const __grid_constant__ CUtensorMap tmx, const T* __restrict__ x, const float* __restrict__ w,
+__device__ __forceinline__ void dw_fwd_body(
+    const CUtensorMap& tmx, const T* __restrict__ x, const float* __restrict__ w,
     T* __restrict__ y, FastDiv fc, int H, int W, FastDiv ftx, FastDiv fty, int64_t num_tiles,
     int clamp, int vec, int flip, int use_tma, int* err) {
   using G = Geo<K>;
@@ -718,6 +718,29 @@ __global__ void __launch_bounds__(kThreads) dw_fwd_kernel(
   // after an abort: let a TMA load still in flight land (bounded) before exiting
   if (*s_abort && use_tma && t + gridDim.x < num_tiles)
     mbar_wait(bars + (sb ^ 1), (phase >> (sb ^ 1)) & 1u);
+}
+
+template <typename T, int K, int PY>
+__global__ void __launch_bounds__(kThreads) dw_fwd_kernel(
+    const __grid_constant__ CUtensorMap tmx, const T* __restrict__ x, const float* __restrict__ w,
+    T* __restrict__ y, FastDiv fc, int H, int W, FastDiv ftx, FastDiv fty, int64_t num_tiles,
+    int clamp, int vec, int flip, int use_tma, int* err) {
+  dw_fwd_body<T, K, PY>(tmx, x, w, y, fc, H, W, ftx, fty, num_tiles, clamp, vec, flip, use_tma,
+                        err);
+}
+
+// The same pass compiled for five CTAs per SM (at most 51 registers).  Used
+// for FP32 K = 7 one tile per CTA, where it fits in 48 registers and 38.5 KB
+// of shared memory and the extra CTA per SM hides more of each CTA's tile
+// load; other sizes keep the default allocation (with this bound K = 3 and 15
+// lose registers they need).
+template <typename T, int K, int PY>
+__global__ void __launch_bounds__(kThreads, 5) dw_fwd_kernel_hi_occ(
+    const __grid_constant__ CUtensorMap tmx, const T* __restrict__ x, const float* __restrict__ w,
+    T* __restrict__ y, FastDiv fc, int H, int W, FastDiv ftx, FastDiv fty, int64_t num_tiles,
+    int clamp, int vec, int flip, int use_tma, int* err) {
+  dw_fwd_body<T, K, PY>(tmx, x, w, y, fc, H, W, ftx, fty, num_tiles, clamp, vec, flip, use_tma,
+                        err);
 }
 
 // ------------------------------------------------------ separable filter

@@ -14,11 +14,27 @@ namespace giga {
 // per CTA and a single shared-memory stage (the kernel's prefetch branch never
 // runs because gridDim.x >= tiles); 1: as many CTAs as fit on the GPU, each
 // with two stages -- an autotuning candidate.
+// The forward kernel of a launch: for FP32 K = 7 with one tile per CTA the
+// five-CTA-per-SM compilation (instantiated for that case only), else the
+// default one.  Raises the kernel's shared-memory limit first.
+template <typename T, int K, int PY>
+static cudaError_t fwd_kernel_for(bool persistent, size_t smem,
+                                  decltype(&dw_fwd_kernel<T, K, PY>)* kern) {
+  if constexpr (sizeof(T) == 4 && K == 7 && PY == 8) {
+    if (!persistent) {
+      *kern = dw_fwd_kernel_hi_occ<T, K, PY>;
+      return set_smem_once<dw_fwd_kernel_hi_occ<T, K, PY>>(smem);
+    }
+  }
+  *kern = dw_fwd_kernel<T, K, PY>;
+  return set_smem_once<dw_fwd_kernel<T, K, PY>>(smem);
+}
+
 template <typename T, int K, int PY>
 static cudaError_t fwd_impl(const DwArgs& a, bool input_grad, bool persistent, cudaStream_t st) {
   using S = FwdShape<K, PY, T>;
-  auto kern = dw_fwd_kernel<T, K, PY>;
-  cudaError_t e = set_smem_once<dw_fwd_kernel<T, K, PY>>((size_t)S::SM_BYTES);
+  decltype(&dw_fwd_kernel<T, K, PY>) kern = nullptr;
+  cudaError_t e = fwd_kernel_for<T, K, PY>(persistent, (size_t)S::SM_BYTES, &kern);
   if (e != cudaSuccess) return e;
   const int64_t tiles_x = (a.W + kTileW - 1) / kTileW;
   const int64_t tiles_y = (a.H + S::TH - 1) / S::TH;
