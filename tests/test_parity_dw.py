@@ -279,3 +279,29 @@ def test_plain_scale_sampled(giga, K):
     assert normwise(got, ref) <= FP32_TOL
     del xc, y
     torch.cuda.empty_cache()
+
+
+def test_bf16_workload_sampled(giga):
+    """32 x 3 x 2048 x 2048 BF16 images, 9 x 9 filters, zero border -- the BF16
+    comparison of the benchmark, in its launch configuration: sampled y and dx
+    pixels (every kind of border pixel included) and a few filter-gradient taps
+    against the oracle on the BF16-rounded inputs (kernel error) and on the
+    FP32 originals (end to end)."""
+    xb, w, dyb, x32, dy32 = workloads.bf16()
+    xc, wc, dyc = xb.cuda(), w.cuda(), dyb.cuda()
+    y = giga.conv2d_fwd(xc, wc, "zero")
+    dx, dw = giga.conv2d_bwd(xc, dyc, wc, "zero")
+    N, C, H, W = xb.shape
+    idx = torch.unique(torch.cat([workloads.sample_indices(xb.numel(), 2000, salt=9),
+                                  workloads.border_indices(2, C, H, W, per_plane=2, salt=9)]))
+    ii = idx.numpy()
+    xr, dyr = xb.float().numpy(), dyb.float().numpy()   # the BF16-rounded inputs
+    for out, fn, a_r, a_32 in ((y, oracle.dw_fwd_points, xr, x32.numpy()),
+                               (dx, oracle.dw_bwd_input_points, dyr, dy32.numpy())):
+        got = out.reshape(-1)[idx.cuda()].double().cpu().numpy()
+        assert normwise(got, fn(a_r, w.numpy(), oracle.ZERO, ii)) <= BF16_KERNEL_TOL
+        assert normwise(got, fn(a_32, w.numpy(), oracle.ZERO, ii)) <= BF16_E2E_TOL
+    taps = np.array([0, 40, 80, 81 + 17, 2 * 81 + 80])
+    ref_dw = oracle.dw_bwd_filter_taps(xr, dyr, 9, oracle.ZERO, taps)
+    got_dw = to_np(dw).reshape(-1)[taps]
+    assert np.abs(got_dw - ref_dw).max() <= FP32_TOL * np.abs(ref_dw).max()

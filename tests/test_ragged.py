@@ -181,6 +181,50 @@ def test_run_requires_the_uploaded_workspace(giga):
     plan.close()
 
 
+@pytest.mark.gpu
+def test_ragged_workload_sampled(giga):
+    """The benchmark's ragged batch (256 three-channel images, sides 64-4096,
+    K in {3, 5, 9, 11}, zero border, inputs drawn on the device as the
+    benchmark draws them) in one autotuned persistent launch: every output is
+    written, and every 16th image is checked on sampled y and dx pixels (every
+    kind of border pixel included) and on filter-gradient taps."""
+    shapes = workloads.ragged_shapes()
+    imgs = []
+    for i, (h, w_, k) in enumerate(shapes):
+        g = workloads.generator("ragged", salt=i + 1, device="cuda")
+        x = torch.rand((3, h, w_), generator=g, device="cuda")
+        wt = torch.randn((3, k, k), generator=g, device="cuda") * 0.1
+        dy = torch.randn((3, h, w_), generator=g, device="cuda")
+        imgs.append({"x": x, "dy": dy, "w": wt, "y": torch.full_like(x, float("nan")),
+                     "dx": torch.full_like(x, float("nan")),
+                     "dw": torch.full((3, k, k), float("nan"), device="cuda")})
+    plan = giga.BatchedPlan(imgs, ALL, "zero")
+    plan.upload()
+    plan.autotune()
+    for t in imgs:
+        for key in ("y", "dx", "dw"):
+            t[key].fill_(float("nan"))
+    plan.run()
+    torch.cuda.synchronize()
+    assert not any(torch.isnan(t[key]).any().item() for t in imgs for key in ("y", "dx", "dw"))
+    for i in range(0, len(shapes), 16):
+        h, w_, k = shapes[i]
+        t = imgs[i]
+        x, dyn, wn = t["x"].cpu()[None].numpy(), t["dy"].cpu()[None].numpy(), t["w"].cpu().numpy()
+        idx = torch.unique(torch.cat([workloads.sample_indices(x.size, 300, salt=i),
+                                      workloads.border_indices(1, 3, h, w_, 1, salt=i)]))
+        ii = idx.numpy()
+        got_y = t["y"].reshape(-1)[idx.cuda()].double().cpu().numpy()
+        got_dx = t["dx"].reshape(-1)[idx.cuda()].double().cpu().numpy()
+        assert normwise(got_y, oracle.dw_fwd_points(x, wn, oracle.ZERO, ii)) <= FP32_TOL, i
+        assert normwise(got_dx, oracle.dw_bwd_input_points(dyn, wn, oracle.ZERO, ii)) <= FP32_TOL, i
+        taps = np.array([0, k * k // 2, k * k + 1, 3 * k * k - 1])
+        ref_dw = oracle.dw_bwd_filter_taps(x, dyn, k, oracle.ZERO, taps)
+        got_dw = to_np(t["dw"]).reshape(-1)[taps]
+        assert np.abs(got_dw - ref_dw).max() <= FP32_TOL * np.abs(ref_dw).max(), i
+    plan.close()
+
+
 # ------------------------------------------------------- host-side checks
 
 def _img(lib, H=10, W=10, C=1, K=3, p=0x100000):
