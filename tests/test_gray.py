@@ -10,7 +10,8 @@ import pytest
 import torch
 
 import oracle
-from helpers import BF16_KERNEL_TOL, assert_fp32, normwise, poison_like, to_np
+import workloads
+from helpers import BF16_KERNEL_TOL, FP32_TOL, assert_fp32, normwise, poison_like, to_np
 
 pytestmark = pytest.mark.gpu
 
@@ -76,3 +77,17 @@ def test_gray_rejects_wrong_channels(giga):
     d = _lib.desc(1, 4, 1, 8, 8, 3, 1, 0, _lib.GIGA_F32, _lib.GIGA_LAYOUT_NCHW)
     assert _lib.giga_gray_conv2d_fwd(d, x.data_ptr(), x.data_ptr(), x.data_ptr(), None) == \
         _lib.GIGA_ERR_INVALID_ARG
+
+
+def test_gray_workload_full_size(giga):
+    """8 RGB images of 4096 x 4096 FP32 with the paper's 3 x 3 Laplacian, zero
+    border, in one launch as the benchmark runs it: images 0 and 7 compared
+    with the oracle in full."""
+    x, _ = workloads.plain_scale(3)   # read as R, G, B planes
+    lap = torch.tensor([[[-1.0, -1, -1], [-1, 8, -1], [-1, -1, -1]]])
+    y = giga.gray_conv2d(x.cuda(), lap.cuda(), "zero")
+    for n in (0, 7):
+        ref = oracle.gray_dw_fwd(x[n:n + 1].numpy(), lap.numpy(), oracle.ZERO)
+        mag = oracle.gray_dw_fwd(x[n:n + 1].numpy(), np.abs(lap.numpy()), oracle.ZERO)
+        assert_fp32(to_np(y[n:n + 1]), ref, mag, 9 + 4, ("image", n))
+        assert normwise(to_np(y[n:n + 1]), ref) <= FP32_TOL

@@ -101,9 +101,9 @@ def test_invalid_scale_and_k(giga):
         giga.upsample_conv2d(x, w, 2)
 
 
-@pytest.mark.parametrize("scale", [2, 4])
+@pytest.mark.parametrize("scale", [2, 4, 8])
 def test_4k_image_sampled(giga, scale):
-    """A 3 x 2160 x 3840 image (the paper's 4K input) upsampled by 2 and 4 and
+    """A 3 x 2160 x 3840 image (the paper's 4K input) upsampled by 2, 4 and 8 and
     filtered with the paper's Laplacian, zero border, as the benchmark runs it:
     sampled outputs and every kind of border pixel."""
     gen = torch.Generator().manual_seed(2504 + 6)
