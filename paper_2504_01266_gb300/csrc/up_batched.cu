@@ -59,7 +59,7 @@ struct UpRagParams {
 // One tile per CTA: CTA b runs tile tile0 + b, a tile of an image with filter
 // size K.  Shared memory as in the single-image kernel (one stage).
 template <typename T, int K>
-__global__ void __launch_bounds__(kThreads) up_rag_kernel(UpRagParams p) {
+__device__ __forceinline__ void up_rag_body(const UpRagParams& p) {
   using U = UpShape<K>;
   using G = Geo<K>;
   extern __shared__ __align__(16) float smem[];
@@ -100,6 +100,17 @@ __global__ void __launch_bounds__(kThreads) up_rag_kernel(UpRagParams p) {
   up_tile<T, K>(sx, U::ZERO_OFF, scol, rowoff, sw, ss, U::SRC_COLS, ty0, tx0, su0, sv0, nr, im.Ho,
                 im.Wo, im.fs, p.clamp != 0, static_cast<T*>(im.y) + (int64_t)plane * im.Ho * im.Wo,
                 im.vec != 0);
+}
+
+template <typename T, int K>
+__global__ void __launch_bounds__(kThreads) up_rag_kernel(UpRagParams p) {
+  up_rag_body<T, K>(p);
+}
+
+// FP32 K = 3 compiled for five CTAs per SM, as the single-image pass.
+template <typename T, int K>
+__global__ void __launch_bounds__(kThreads, 5) up_rag_kernel_hi_occ(UpRagParams p) {
+  up_rag_body<T, K>(p);
 }
 
 }  // namespace giga
@@ -228,9 +239,14 @@ giga_status_t check_up_ws(const giga_upsample_batched_plan_s* plan, void* ws, si
 template <typename T, int K>
 cudaError_t up_rag_launch_k(const UpRagParams& p, int n_tiles, cudaStream_t st) {
   const size_t smem = (size_t)UpShape<K>::SM_FLOATS_1 * 4;
-  cudaError_t e = set_smem_once<up_rag_kernel<T, K>>(smem);
-  if (e != cudaSuccess) return e;
-  up_rag_kernel<T, K><<<n_tiles, kThreads, smem, st>>>(p);
+  cudaError_t e;
+  if constexpr (sizeof(T) == 4 && K == 3) {
+    if ((e = set_smem_once<up_rag_kernel_hi_occ<T, K>>(smem)) != cudaSuccess) return e;
+    up_rag_kernel_hi_occ<T, K><<<n_tiles, kThreads, smem, st>>>(p);
+  } else {
+    if ((e = set_smem_once<up_rag_kernel<T, K>>(smem)) != cudaSuccess) return e;
+    up_rag_kernel<T, K><<<n_tiles, kThreads, smem, st>>>(p);
+  }
   note_launch();
   return cudaGetLastError();
 }

@@ -65,12 +65,10 @@ __global__ void __launch_bounds__(256) up_nearest_kernel(const T* __restrict__ x
 // stages -- those of the next tile are copied while this one is computed --
 // then up_tile expands them along the columns and filters the tile.
 template <typename T, int K>
-__global__ void __launch_bounds__(kThreads) up_fwd_kernel(const T* __restrict__ x,
-                                                          const float* __restrict__ w,
-                                                          T* __restrict__ y, FastDiv fc, int H,
-                                                          int W, int Ho, int Wo, FastDiv fs,
-                                                          FastDiv ftx, FastDiv fty,
-                                                          int64_t num_tiles, int clamp, int vec) {
+__device__ __forceinline__ void up_fwd_body(const T* __restrict__ x, const float* __restrict__ w,
+                                            T* __restrict__ y, FastDiv fc, int H, int W, int Ho,
+                                            int Wo, FastDiv fs, FastDiv ftx, FastDiv fty,
+                                            int64_t num_tiles, int clamp, int vec) {
   using G = Geo<K>;
   using U = UpShape<K>;
   extern __shared__ __align__(16) float smem[];
@@ -141,11 +139,46 @@ __global__ void __launch_bounds__(kThreads) up_fwd_kernel(const T* __restrict__ 
 }
 
 template <typename T, int K>
+__global__ void __launch_bounds__(kThreads) up_fwd_kernel(const T* __restrict__ x,
+                                                          const float* __restrict__ w,
+                                                          T* __restrict__ y, FastDiv fc, int H,
+                                                          int W, int Ho, int Wo, FastDiv fs,
+                                                          FastDiv ftx, FastDiv fty,
+                                                          int64_t num_tiles, int clamp, int vec) {
+  up_fwd_body<T, K>(x, w, y, fc, H, W, Ho, Wo, fs, ftx, fty, num_tiles, clamp, vec);
+}
+
+// The same pass compiled for five CTAs per SM (48 registers): used for FP32
+// K = 3 -- the paper's Laplacian, where the pass is bound by staging and
+// integer work rather than FMAs -- since the fifth CTA hides more of each
+// tile's staging latency (scale 2: 0.127 -> 0.116 ms on a 4K image).
+template <typename T, int K>
+__global__ void __launch_bounds__(kThreads, 5) up_fwd_kernel_hi_occ(
+    const T* __restrict__ x, const float* __restrict__ w, T* __restrict__ y, FastDiv fc, int H,
+    int W, int Ho, int Wo, FastDiv fs, FastDiv ftx, FastDiv fty, int64_t num_tiles, int clamp,
+    int vec) {
+  up_fwd_body<T, K>(x, w, y, fc, H, W, Ho, Wo, fs, ftx, fty, num_tiles, clamp, vec);
+}
+
+// The kernel of a launch (the five-CTA compilation for FP32 K = 3, instantiated
+// for that case only); raises its shared-memory limit first.
+template <typename T, int K>
+static cudaError_t up_kernel_for(size_t smem, decltype(&up_fwd_kernel<T, K>)* kern) {
+  if constexpr (sizeof(T) == 4 && K == 3) {
+    *kern = up_fwd_kernel_hi_occ<T, K>;
+    return set_smem_once<up_fwd_kernel_hi_occ<T, K>>(smem);
+  } else {
+    *kern = up_fwd_kernel<T, K>;
+    return set_smem_once<up_fwd_kernel<T, K>>(smem);
+  }
+}
+
+template <typename T, int K>
 static cudaError_t up_fwd_impl(const UpArgs& a, cudaStream_t st) {
   using U = UpShape<K>;
   const size_t smem = (size_t)U::SM_FLOATS * 4;
-  auto kern = up_fwd_kernel<T, K>;
-  cudaError_t e = set_smem_once<up_fwd_kernel<T, K>>(smem);
+  decltype(&up_fwd_kernel<T, K>) kern = nullptr;
+  cudaError_t e = up_kernel_for<T, K>(smem, &kern);
   if (e != cudaSuccess) return e;
   const int64_t tiles_x = (a.Wo + kTileW - 1) / kTileW;
   const int64_t tiles_y = (a.Ho + U::TH - 1) / U::TH;
