@@ -132,7 +132,7 @@ __global__ void dw_fold_rows_kernel(const float* __restrict__ dy, const float* _
 
 __global__ void dw_fold_cols_kernel(const float* __restrict__ dy, const float* __restrict__ w,
                                     float* __restrict__ dx, int C, int H, int W, int K) {
-  extern __shared__ float tab[];  // Wl[r][K], Wr[r][K], corners 4 x r x r
+  extern __shared__ float tab[];  // Wl[r][K], Wr[r][K], corners 4 x r x r, two row strips
   const int r = (K - 1) / 2;
   const int64_t plane = blockIdx.y;
   const float* f = w + (plane % C) * (int64_t)K * K;
@@ -168,16 +168,31 @@ __global__ void dw_fold_cols_kernel(const float* __restrict__ dy, const float* _
     Cbl[k] = bl;
     Cbr[k] = br;
   }
-  __syncthreads();
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= H) return;
+  // the block's rows p0 - r .. p0 + blockDim.x - 1 + r of the first and the
+  // last r columns, staged once (neighbouring threads share K - 1 of their K
+  // rows; reading them from global memory per thread was latency-bound)
   const float* g = dy + plane * (int64_t)H * W;
   const int cols = min(r, W), rows = min(r, H);
+  const int p0 = blockIdx.x * blockDim.x;
+  const int strip_rows = blockDim.x + 2 * r;
+  float* sl = Cbr + r * r;           // [strip_rows][r]: columns 0 .. r - 1
+  float* sr = sl + strip_rows * r;   // [strip_rows][r]: columns W - 1 .. W - r
+  for (int k = threadIdx.x; k < strip_rows * r; k += blockDim.x) {
+    const int i = k / r, j = k - (k / r) * r;
+    const int row = p0 - r + i;
+    sl[k] = j < cols ? dy_at(g, H, W, row, j) : 0.f;
+    sr[k] = j < cols ? dy_at(g, H, W, row, W - 1 - j) : 0.f;
+  }
+  __syncthreads();
+  const int p = p0 + threadIdx.x;
+  if (p >= H) return;
   float left = 0.f, right = 0.f;
   for (int j = 0; j < cols; ++j)
     for (int a = 0; a < K; ++a) {
-      left = fmaf(Wl[j * K + a], dy_at(g, H, W, p - a + r, j), left);
-      right = fmaf(Wr[j * K + a], dy_at(g, H, W, p - a + r, W - 1 - j), right);
+      // dy row p - a + r sits at strip row threadIdx.x + 2r - a
+      const int i = threadIdx.x + 2 * r - a;
+      left = fmaf(Wl[j * K + a], sl[i * r + j], left);
+      right = fmaf(Wr[j * K + a], sr[i * r + j], right);
     }
   // corner sums belong to the pixels of the first / last row
   if (p == 0 || p == H - 1) {
@@ -215,9 +230,11 @@ cudaError_t dw_fixup_launch(const DwArgs& a, cudaStream_t st) {
     note_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    dw_fold_cols_kernel<<<grid_cols, kFoldThreads, sizeof(float) * (2 * r * a.K + 4 * r * r),
-                          st>>>(static_cast<const float*>(a.dy), a.w, static_cast<float*>(a.dx),
-                                (int)a.C, (int)a.H, (int)a.W, a.K);
+    const size_t cols_smem =
+        sizeof(float) * (2 * r * a.K + 4 * r * r + 2 * (kFoldThreads + 2 * r) * r);
+    dw_fold_cols_kernel<<<grid_cols, kFoldThreads, cols_smem, st>>>(
+        static_cast<const float*>(a.dy), a.w, static_cast<float*>(a.dx), (int)a.C, (int)a.H,
+        (int)a.W, a.K);
     note_launch();
     return cudaGetLastError();
   }
