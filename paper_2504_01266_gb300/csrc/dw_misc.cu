@@ -267,9 +267,18 @@ __global__ void dw_finalize_kernel(const float* __restrict__ partials, float* __
   const int c = (int)(gw / KK), k = (int)(gw % KK);
   double s = 0.0;
   const int64_t count = N * chunks;
+  // idx = n * chunks + ch advances by 32 = step_n * chunks + step_ch: one
+  // division per lane instead of a 64-bit division per partial
+  int64_t n = lane / chunks, ch = lane - (lane / chunks) * chunks;
+  const int64_t step_n = 32 / chunks, step_ch = 32 - step_n * chunks;
   for (int64_t idx = lane; idx < count; idx += 32) {
-    const int64_t n = idx / chunks, ch = idx - n * chunks;
     s += (double)partials[((n * C + c) * chunks + ch) * KK + k];
+    n += step_n;
+    ch += step_ch;
+    if (ch >= chunks) {
+      ch -= chunks;
+      ++n;
+    }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
