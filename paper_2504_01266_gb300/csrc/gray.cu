@@ -26,16 +26,18 @@ __device__ __forceinline__ float gray_of(float r, float g, float b) {
 }
 
 // ------------------------------------------------------------ conversion
+// Image n = blockIdx.y, + gridDim.y, ...; pixels grid-strided along x (no
+// division per pixel).
 template <typename T>
 __global__ void __launch_bounds__(256) gray_kernel(const T* __restrict__ x, T* __restrict__ y,
                                                    int64_t P, int64_t N) {
-  const int64_t total = N * P;
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total;
-       k += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t n = k / P, p = k - n * P;
-    const T* px = x + n * 3 * P + p;
-    Elem<T>::store(y + k, gray_of(Elem<T>::load(px), Elem<T>::load(px + P),
-                                  Elem<T>::load(px + 2 * P)));
+  for (int64_t n = blockIdx.y; n < N; n += gridDim.y) {
+    const T* xn = x + n * 3 * P;
+    T* yn = y + n * P;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < P;
+         p += (int64_t)gridDim.x * blockDim.x)
+      Elem<T>::store(yn + p, gray_of(Elem<T>::load(xn + p), Elem<T>::load(xn + P + p),
+                                     Elem<T>::load(xn + 2 * P + p)));
   }
 }
 
@@ -202,8 +204,13 @@ cudaError_t gray_fwd_launch(const GrayArgs& a, cudaStream_t st) {
 }
 
 cudaError_t gray_launch(const GrayArgs& a, cudaStream_t st) {
-  const int64_t P = a.H * a.W, total = a.N * P;
-  const int grid = (int)std::min<int64_t>((total + 255) / 256, (int64_t)sm_count() * 16);
+  const int64_t P = a.H * a.W;
+  // about 16 CTAs of 256 threads per SM in all, split between images (y) and
+  // the pixels of an image (x)
+  const int64_t budget = (int64_t)sm_count() * 16;
+  const int64_t gy = std::min<int64_t>(a.N, 65535);
+  const int64_t gx = std::max<int64_t>(1, std::min<int64_t>((P + 255) / 256, budget / gy + 1));
+  const dim3 grid((unsigned)gx, (unsigned)gy);
   if (a.dtype == 0)
     gray_kernel<float><<<grid, 256, 0, st>>>(static_cast<const float*>(a.x),
                                              static_cast<float*>(a.y), P, a.N);
