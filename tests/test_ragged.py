@@ -262,3 +262,33 @@ def test_plan_workspace_size_covers_table_and_partials():
     partial_floats = 3 * 2 * 25 + 3 * 1 * 225
     assert n >= partial_floats * 4 + (3 * 2 + 3) * 16 and n % 256 == 0
     assert tiles0 == 6
+
+
+def test_plan_workspace_covers_every_chunk_size_and_autotune_argument_checks():
+    """The plan's workspace is sized for the smallest chunks (one tile each),
+    so the autotuner can switch chunk sizes inside it; the tuner's argument
+    checks run before any CUDA call."""
+    from paper_2504_01266_gb300 import _lib, build
+    build.build()
+    arr = (_lib.giga_image_t * 2)(_img(_lib, H=100, W=300, C=3, K=5),
+                                  _img(_lib, H=64, W=128, C=3, K=15))
+    n = _lib.giga_conv2d_batched_workspace_size(arr, 2, ALL)
+    # one tile per chunk: 6 chunks per channel for image 0, 1 for image 1
+    partial_floats = 3 * 6 * 25 + 3 * 1 * 225
+    chunks = 3 * 6 + 3 * 1
+    assert n >= partial_floats * 4 + chunks * 16 and n % 256 == 0
+    plan = _lib.giga_batched_plan_create(arr, 2, ALL, 0, 0)
+    assert _lib.giga_batched_plan_workspace_size(plan) == n
+    assert _lib.giga_batched_plan_tiles_per_chunk(plan) == 4
+    lib = _lib.load()
+    assert lib.giga_batched_plan_autotune(None, 0x10000, n, None, None) == \
+        _lib.GIGA_ERR_INVALID_ARG
+    assert lib.giga_batched_plan_autotune(plan, None, n, None, None) == _lib.GIGA_ERR_WORKSPACE
+    assert lib.giga_batched_plan_autotune(plan, 0x10000, n - 1, None, None) == \
+        _lib.GIGA_ERR_WORKSPACE
+    assert lib.giga_batched_plan_autotune(plan, 0x10010, n, None, None) == \
+        _lib.GIGA_ERR_WORKSPACE
+    # never uploaded: run refuses before any launch
+    assert _lib.giga_batched_plan_run(plan, 0x10000, n, None) == _lib.GIGA_ERR_INVALID_ARG
+    assert _lib.giga_batched_plan_tiles_per_chunk(None) == -1
+    _lib.giga_batched_plan_destroy(plan)
