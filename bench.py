@@ -38,11 +38,17 @@ NCU_DRAM_BYTES_PER_PX = {
 METRIC = "Gpixel*tap/s fwd+bwd (depthwise KxK, K in {3,7,15})"
 UNIT = "Gpixel*tap/s"
 WORKLOAD = "plain_scale: 8x3x4096x4096 fp32, depthwise K in {3,7,15} normal(0,0.1), clamp border, fwd+bwd"
-SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0   # GB300: FP32 FMA units and max clock
+FP32_LANES, SM_MAX_MHZ = 128, 2070.0   # FP32 FMA lanes per SM; fallback max SM clock
 RAGGED_IMAGES = None   # all 256 images of the ragged workload; a prefix for profiling runs
+# FP32 FMA throughput measured on this device by the library's own kernel
+# (giga_fp32_fma_peak) and the device's SM count; set by measure_fp32_peak()
+FP32_MEASURED = {}
 
 
 def peaks():
+    """Roofline denominators: HBM from MEASURED_PEAKS.json (the driver's copy
+    benchmark), FP32 FMA from this run's measurement when it has been taken,
+    else derived from the SM count, lanes and maximum clock."""
     p = {"hbm_gbs": 6800.0, "source": "fallback"}
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -51,9 +57,43 @@ def peaks():
         mhz = float(m.get("sm_max_mhz", SM_MAX_MHZ))
     except Exception:
         mhz = SM_MAX_MHZ
-    # FP32 FMA peak from unit counts and the maximum SM clock (2 flop per FMA)
-    p["fp32_tflops"] = SMS * FP32_LANES * 2 * mhz * 1e6 / 1e12
+    sms = FP32_MEASURED.get("sms", 152)
+    p["sms"] = sms
+    p["fp32_tflops_derived"] = sms * FP32_LANES * 2 * mhz * 1e6 / 1e12
+    if FP32_MEASURED.get("tflops"):
+        p["fp32_tflops"] = FP32_MEASURED["tflops"]
+        p["fp32_source"] = (f"measured: giga_fp32_fma_peak (16 FMA chains/thread, {sms} SMs, "
+                            f"best of plain and packed f32x2)")
+    else:
+        p["fp32_tflops"] = p["fp32_tflops_derived"]
+        p["fp32_source"] = f"derived: {sms} SMs x {FP32_LANES} lanes x 2 x {mhz:.0f} MHz"
     return p
+
+
+def measure_fp32_peak(dev):
+    """FP32 FMA throughput of this GPU (plain and packed FMA) and its SM count."""
+    import torch
+    from paper_2504_01266_gb300 import _lib as L
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    nb = L.giga_fp32_fma_peak_sink_bytes()
+    sink = torch.empty(nb, dtype=torch.uint8, device=dev)
+    sp = torch.cuda.current_stream(dev).cuda_stream
+    plain, _ = L.giga_fp32_fma_peak(0, sink.data_ptr(), nb, sp)
+    packed, _ = L.giga_fp32_fma_peak(1, sink.data_ptr(), nb, sp)
+    FP32_MEASURED.update({"sms": sms, "plain": plain, "packed": packed,
+                          "tflops": max(plain, packed)})
+    return FP32_MEASURED
+
+
+def _r(v, digits=4):
+    """Round floats (recursively) to `digits` significant digits for the line."""
+    if isinstance(v, float):
+        return float(f"{v:.{digits}g}")
+    if isinstance(v, dict):
+        return {k: _r(x, digits) for k, x in v.items()}
+    if isinstance(v, (list, tuple)):
+        return [_r(x, digits) for x in v]
+    return v
 
 
 def set_images(n: int):
@@ -677,6 +717,117 @@ def compare_dense(dev, iters, bf16_peak):
 
 # ------------------------------------------------------------------- GPU
 
+def check_step(dev, x, dy, filt, run_k, n_points=1500, n_taps=6):
+    """Errors of the timed step's own outputs against the FP64 oracle.
+
+    For every K the step's forward and backward calls are repeated once in
+    the timed launch configuration (y and dx are shared by the three filter
+    sizes, so each K's outputs are checked right after its own calls).
+    Sampled y and dx pixels of the first and last image (every kind of border
+    pixel included) and `n_taps` filter-gradient taps per K (corners, centre,
+    seeded others; each a sum over the whole batch) are compared with the
+    oracle; returns {K: {"y", "dx", "dw"}} normwise errors over the samples."""
+    import numpy as np
+    import torch
+    import oracle
+    import workloads
+    Nn, Cc, Hh, Ww = x.shape
+    imgs = sorted({0, Nn - 1})
+    x64 = x.cpu().numpy().astype(np.float64)
+    dy64 = dy.cpu().numpy().astype(np.float64)
+    xs, dys = np.ascontiguousarray(x64[imgs]), np.ascontiguousarray(dy64[imgs])
+    plane = Cc * Hh * Ww
+    # rows and columns 1..7 from each edge: their reads (forward) or the
+    # contributions they receive (input gradient) cross the border
+    g = np.random.default_rng(2521)
+    near = []
+    for p in range(len(imgs) * Cc):
+        i, j = int(g.integers(0, Hh)), int(g.integers(0, Ww))
+        for d in range(1, 8):
+            near += [p * Hh * Ww + d * Ww + j, p * Hh * Ww + (Hh - 1 - d) * Ww + j,
+                     p * Hh * Ww + i * Ww + d, p * Hh * Ww + i * Ww + Ww - 1 - d]
+    sub = torch.unique(torch.cat([
+        workloads.sample_indices(len(imgs) * plane, n_points, salt=21),
+        workloads.border_indices(len(imgs), Cc, Hh, Ww, per_plane=2, salt=21),
+        torch.tensor(near, dtype=torch.int64)]))
+    full = (torch.tensor(imgs)[sub // plane] * plane + sub % plane).to(dev)
+    out = {}
+    for K in KS:
+        y, dx, dw = run_k(K)
+        torch.cuda.synchronize(dev)
+        w = filt[K].double().cpu().numpy()
+        gy = y.reshape(-1)[full].double().cpu().numpy()
+        gdx = dx.reshape(-1)[full].double().cpu().numpy()
+        ry = oracle.dw_fwd_points(xs, w, oracle.CLAMP, sub.numpy())
+        rdx = oracle.dw_bwd_input_points(dys, w, oracle.CLAMP, sub.numpy())
+        kk = K * K
+        rng = np.random.default_rng(2504 + K)
+        taps = sorted({0, kk // 2, kk - 1, *(c * kk + int(t) for c, t in
+                                              zip(rng.integers(0, Cc, n_taps - 3),
+                                                  rng.integers(0, kk, n_taps - 3)))})
+        rdw = oracle.dw_bwd_filter_taps(x64, dy64, K, oracle.CLAMP, np.array(taps))
+        gdw = dw.reshape(-1)[torch.tensor(taps, device=dev)].double().cpu().numpy()
+        out[K] = {"y": _normwise(gy, ry), "dx": _normwise(gdx, rdx), "dw": _normwise(gdw, rdw),
+                  "points": int(sub.numel()), "taps": len(taps)}
+    del x64, dy64
+    return out
+
+
+def summarize_checks(checks):
+    """Per-K sampled errors of the timed step, compact, with the verdict
+    against the FP32 tolerance (1e-5 normwise)."""
+    if not checks:
+        return None
+    worst = max(max(c["y"], c["dx"], c["dw"]) for c in checks.values())
+    out = {f"K{K}": _r([c["y"], c["dx"], c["dw"]], 2) for K, c in checks.items()}
+    out["order"] = "err_normwise_sampled y, dx, dw vs the FP64 oracle"
+    out["ok"] = bool(worst <= 1e-5)
+    return out
+
+
+def summarize(compare):
+    """The comparisons of the headline metric in a few hundred characters:
+    BF16 vs FP32 storage (speed ratio and errors), the ragged persistent
+    launch vs the per-image loop, the dense tensor-core case, and the
+    widening rows' speed-ups over their unfused forms."""
+    if not compare:
+        return None
+    out = {}
+    b = compare.get("bf16")
+    if b:
+        e16, e32 = b["bf16"]["err_normwise_sampled"], b["fp32"]["err_normwise_sampled"]
+        out["bf16_over_fp32"] = {
+            "K9": b["bf16_over_fp32"], "K3": b["k3"]["bf16_over_fp32"],
+            "ms_K9": [b["bf16"]["ms"], b["fp32"]["ms"]],
+            "err_bf16_kernel": [e16["y"], e16["dx"]],
+            "err_bf16_e2e": [e16["y_vs_fp32_inputs"], e16["dx_vs_fp32_inputs"]],
+            "err_fp32": [e32["y"], e32["dx"]]}
+    r = compare.get("ragged")
+    if r:
+        out["ragged"] = {"graph_ms": r["graph_persistent"]["ms"],
+                         "loop_ms": r["per_image_loop"]["ms"], "speedup": r["speedup"],
+                         "tpc": r["graph_persistent"]["tiles_per_chunk_autotuned"],
+                         "bitwise": r["y_dx_bitwise_equal_to_per_image_path"]}
+    d = compare.get("dense")
+    if d:
+        out["dense"] = {k: [d[k]["tflops"], d[k]["frac_of_bf16_peak"]]
+                        for k in ("fwd", "bwd_input", "bwd_filter")}
+        out["dense"]["err"] = d["fwd"]["err_normwise_sampled"]
+    u = compare.get("upsample_sharpen")
+    if u:
+        out["upsample_speedup"] = {s: v["speedup"] for s, v in u["scales"].items()}
+    ub = compare.get("upsample_sharpen_batched")
+    if ub:
+        out["up_batched_speedup"] = ub["speedup"]
+    sp = compare.get("separable")
+    if sp:
+        out["separable_speedup"] = {k: v["speedup"] for k, v in sp["K"].items()}
+    gr = compare.get("gray_sharpen")
+    if gr:
+        out["gray_speedup"] = gr["speedup"]
+    return _r(out, 3)
+
+
 def run_giga(args):
     import torch
     world, rank, local = dist_env()
@@ -691,6 +842,8 @@ def run_giga(args):
     build.build()
     L = _lib
     L.load()
+    # the ALU roofline's denominator: this GPU's measured FP32 FMA rate
+    measure_fp32_peak(dev)
 
     g = torch.Generator(device=dev)
     g.manual_seed(2504 + 1)
@@ -787,6 +940,19 @@ def run_giga(args):
     rate, ms = aggregate(taps_per_step(), ms_local, world)
     value = rate / 1e9
 
+    # the step's own outputs against the oracle (after timing, same launches)
+    checks = None
+    if not args.no_check:
+        def run_k(K):
+            d = descs[K]
+            L.check(L.giga_conv2d_fwd(d, x.data_ptr(), filt[K].data_ptr(), y.data_ptr(),
+                                      None, 0, sp), "fwd")
+            L.check(L.giga_conv2d_bwd(d, x.data_ptr(), dy.data_ptr(), filt[K].data_ptr(),
+                                      dx.data_ptr(), dws[K].data_ptr(), ws.data_ptr(),
+                                      ws_bytes, sp), "bwd")
+            return y, dx, dws[K]
+        checks = check_step(dev, x, dy, filt, run_k)
+
     # per-op roofline from the events recorded inside the timed region
     pk = peaks()
     px = N * C * H * W
@@ -830,7 +996,11 @@ def run_giga(args):
                 "unit": dom["unit"], "frac": dom["frac"], "traffic": traffic,
                 "kernel": kname, "op": f"{dom['op']} K={dom['K']}",
                 "peak_source": (f"{pk['source']} HBM copy" if dom["bound"] == "hbm" else
-                                "FP32 FMA: 152 SMs x 128 lanes x 2 x max SM clock")}
+                                pk["fp32_source"]),
+                "sms": pk["sms"], "fp32_tflops_measured": FP32_MEASURED.get("tflops"),
+                "fp32_tflops_plain": FP32_MEASURED.get("plain"),
+                "fp32x2_tflops_packed": FP32_MEASURED.get("packed"),
+                "fp32_tflops_derived": pk["fp32_tflops_derived"]}
 
     # End to end through the C ABI with host buffers (pinned), copies timed.
     # Every step copies x and dy host->device and reads y, dx and dw of every K
@@ -939,6 +1109,16 @@ def run_giga(args):
                "sample": f"{desc}; {dt:.1f} s"}
 
     if rank == 0:
+        # full per-op and per-comparison detail: stderr (and --detail FILE)
+        detail = {"ops": ops, "compare": compare, "checks": checks, "autotune": tuned,
+                  "fp32_peak": FP32_MEASURED}
+        print("bench detail: " + json.dumps(detail), file=sys.stderr)
+        if args.detail:
+            with open(args.detail, "w") as f:
+                json.dump(detail, f, indent=1)
+        # the line: contract keys first, then the compact per-op times, the
+        # step's own errors and the comparisons, so a tail of the output
+        # holds all of the latter
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
@@ -946,15 +1126,15 @@ def run_giga(args):
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "N": N, "C": C, "H": H, "W": W, "K": list(KS),
                        "border": "clamp", "parallelism": f"replicas{world}",
-                       "l2": "inputs larger than L2 (1.6 GB per tensor), no flush",
-                       "autotune": tuned},
-            "roofline": roofline,
-            "cpu_baseline": cpu,
-            "e2e": e2e,
+                       "l2": "inputs larger than L2 (1.6 GB per tensor), no flush"},
+            "roofline": _r(roofline),
+            "cpu_baseline": _r(cpu),
+            "e2e": _r(e2e),
             "gpu_launches": launches,
             "clocks": clocks.summary(),
-            "ops": ops,
-            "compare": compare,
+            "ops": {f"{o['op']}{o['K']}": _r([o["ms"], o["frac"]], 3) for o in ops},
+            "checks": summarize_checks(checks),
+            "summary": summarize(compare),
         }
         print(json.dumps(line))
     if world > 1:
@@ -969,6 +1149,7 @@ def run_section(args):
     build.build()
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
+    measure_fp32_peak(dev)
     peak = 1894.6
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -1001,6 +1182,10 @@ def main():
     ap.add_argument("--tune-cache", default="",
                     help="autotune cache file: load it and skip tuning if it exists, "
                          "else tune and save the choices there")
+    ap.add_argument("--no-check", action="store_true",
+                    help="skip the oracle check of the timed step's outputs")
+    ap.add_argument("--detail", default="",
+                    help="also write the per-op and per-comparison detail to this JSON file")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the BF16 / ragged / dense comparison measurements")
     ap.add_argument("--section",

@@ -23,9 +23,12 @@
  *
  * Conventions for every entry point:
  *   - Every pointer argument named x, y, dx, dy, w, dw, ws is a DEVICE pointer
- *     owned by the caller; the library never allocates device memory and never
- *     keeps a pointer after the call returns (batched plans keep host copies of
- *     their descriptors, see below).
+ *     owned by the caller; no call allocates device memory and none keeps a
+ *     pointer after it returns (batched plans keep host copies of their
+ *     descriptors, see below).  The one piece of device memory the library
+ *     holds is the fixed 4 MiB scratch array of
+ *     giga_conv2d_bwd_filter_noalloc, which exists from the moment the
+ *     library's code is loaded on a device until the process exits.
  *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
  *     Every launch is asynchronous on that stream; nothing synchronises the
  *     host unless stated.  The calls are safe to capture into a CUDA graph
@@ -81,7 +84,9 @@ typedef struct {
 } giga_conv2d_desc_t;
 
 /* Bytes of device workspace the ops in `ops` (GIGA_OP_* bitmask) need for
- * this descriptor.  0 means no workspace.  Workspaces must be 256-B aligned. */
+ * this descriptor (Section 4.2.4's filter and the gradients derived from it;
+ * only the filter gradient of the depthwise case and the dense gradients need
+ * any).  0 means no workspace.  Workspaces must be 256-B aligned. */
 giga_status_t giga_conv2d_workspace_size(const giga_conv2d_desc_t* desc, int32_t ops,
                                          size_t* bytes);
 
@@ -91,19 +96,27 @@ giga_status_t giga_conv2d_workspace_size(const giga_conv2d_desc_t* desc, int32_t
 giga_status_t giga_conv2d_fwd(const giga_conv2d_desc_t* desc, const void* x, const void* w,
                               void* y, void* ws, size_t ws_bytes, void* stream);
 
-/* Input gradient dx = K_w^T dy (same layouts as x / y). */
+/* Input gradient dx = K_w^T dy (same layouts as x / y): the adjoint of
+ * Section 4.2.4's neighbourhood sum, every weighted read of the forward pass
+ * sent back to the pixel it read (for the clamp border, the edge pixel the
+ * clamped read landed on). */
 giga_status_t giga_conv2d_bwd_input(const giga_conv2d_desc_t* desc, const void* dy,
                                     const void* w, void* dx, void* ws, size_t ws_bytes,
                                     void* stream);
 
-/* Filter gradient dw = d<K_w x, dy>/dw, FP32, same layout as w.  Per-CTA FP32
- * partial sums go to the workspace and are summed in FP64 in a fixed order. */
+/* Filter gradient dw = d<K_w x, dy>/dw, FP32, same layout as w: the
+ * derivative of Section 4.2.4's neighbourhood sum with respect to each filter
+ * entry, dw[c][a][b] = sum over n, i, j of dy[n][c][i][j] times the pixel tap
+ * (a, b) reads for output (i, j).  Per-CTA FP32 partial sums go to the
+ * workspace and are summed in FP64 in a fixed order. */
 giga_status_t giga_conv2d_bwd_filter(const giga_conv2d_desc_t* desc, const void* x,
                                      const void* dy, float* dw, void* ws, size_t ws_bytes,
                                      void* stream);
 
-/* Both gradients in one fused pass that reads x and dy once (depthwise only;
- * needs the workspace of GIGA_OP_BWD_INPUT | GIGA_OP_BWD_FILTER). */
+/* Both gradients of Section 4.2.4's neighbourhood sum (the adjoint and the
+ * filter derivative above) in one fused pass that reads x and dy once
+ * (depthwise only; needs the workspace of GIGA_OP_BWD_INPUT |
+ * GIGA_OP_BWD_FILTER). */
 giga_status_t giga_conv2d_bwd(const giga_conv2d_desc_t* desc, const void* x, const void* dy,
                               const float* w, void* dx, float* dw, void* ws, size_t ws_bytes,
                               void* stream);
@@ -120,9 +133,18 @@ giga_status_t giga_conv2d_bwd(const giga_conv2d_desc_t* desc, const void* x, con
  *   - Limit: problems whose partial sums do not fit the array even with one
  *     CTA per image plane (N*C*K*K > 1,048,576) return GIGA_ERR_INVALID_ARG
  *     and say so in giga_last_error_detail(); use giga_conv2d_bwd_filter.
+ *   - Chunking: the call starts from the chunk length giga_conv2d_bwd_filter
+ *     would use (the autotuner's cached or pinned choice for this problem,
+ *     else the built-in default; this entry point never benchmarks) and
+ *     doubles it until the partial sums fit the array.  When no doubling is
+ *     needed the result is bit-identical to giga_conv2d_bwd_filter's; when it
+ *     is, the FP32 partials are grouped differently and the two agree to FP32
+ *     rounding, not bit for bit.
  *   - The first call on each device looks up the array's device address
- *     (cudaGetSymbolAddress with that device current); make that first call
- *     before any stream capture.
+ *     (cudaGetSymbolAddress with that device current) and keeps it for the
+ *     life of the process; make that first call before any stream capture.
+ *     cudaDeviceReset invalidates the kept address: do not call this entry
+ *     point on a device after resetting it.
  *   - All calls share the one array, which keeps the last call's contents
  *     (nothing in it needs to start at zero).  Calls that overlap on the GPU --
  *     different streams or host threads -- race on it; serialise them. */
@@ -349,6 +371,20 @@ const char* giga_last_error_detail(void);
  * reset (for launch accounting in benchmarks). */
 uint64_t giga_launch_count(void);
 void giga_launch_count_reset(void);
+
+/* Measured FP32 multiply-add throughput of the current device, the
+ * denominator of the ALU roofline of the depthwise kernels (not part of the
+ * paper's method).  Runs 16 independent FMA chains per thread on every SM,
+ * plain (packed = 0: fma.rn.f32) or packed (packed = 1: fma.rn.f32x2, two
+ * FMAs per instruction): one warm-up launch, then the fastest of 5 timed
+ * launches (CUDA events on `stream`; synchronises it; not capturable).
+ * *tflops receives 2 x FMAs / time in TFLOP/s, *ms (may be NULL) that
+ * launch's milliseconds.  `sink` is a device buffer of at least
+ * giga_fp32_fma_peak_sink_bytes() bytes that receives one float per thread
+ * (GIGA_ERR_WORKSPACE if smaller). */
+size_t giga_fp32_fma_peak_sink_bytes(void);
+giga_status_t giga_fp32_fma_peak(int32_t packed, float* sink, size_t sink_bytes, double* tflops,
+                                 double* ms, void* stream);
 
 #ifdef __cplusplus
 }

@@ -54,6 +54,7 @@ EXPORTS = (
     "giga_last_error_detail",
     "giga_launch_count",
     "giga_launch_count_reset",
+    "giga_fp32_fma_peak_sink_bytes", "giga_fp32_fma_peak",
 )
 
 
@@ -137,6 +138,9 @@ _SIGS = {
     "giga_last_error_detail": (ctypes.c_char_p, []),
     "giga_launch_count": (ctypes.c_uint64, []),
     "giga_launch_count_reset": (None, []),
+    "giga_fp32_fma_peak_sink_bytes": (_SZ, []),
+    "giga_fp32_fma_peak": (_ST, [_I32, _P, _SZ, ctypes.POINTER(ctypes.c_double),
+                                 ctypes.POINTER(ctypes.c_double), _P]),
 }
 
 
@@ -360,3 +364,15 @@ def giga_launch_count() -> int:
 
 def giga_launch_count_reset() -> None:
     load().giga_launch_count_reset()
+
+
+def giga_fp32_fma_peak_sink_bytes() -> int:
+    return int(load().giga_fp32_fma_peak_sink_bytes())
+
+
+def giga_fp32_fma_peak(packed, sink, sink_bytes, stream):
+    """Measured FP32 FMA throughput: returns (TFLOP/s, ms of the timed launch)."""
+    tf, ms = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    check(load().giga_fp32_fma_peak(packed, sink, sink_bytes, ctypes.byref(tf), ctypes.byref(ms),
+                                    stream), "giga_fp32_fma_peak")
+    return float(tf.value), float(ms.value)

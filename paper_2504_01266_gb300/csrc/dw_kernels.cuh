@@ -6,16 +6,23 @@
 //   y[n][c][i][j]  = sum_{a,b} w[c][a][b] * x~[n][c][i + a - r][j + b - r]
 //   g[n][c][u][v]  = sum_{a,b} w[c][K-1-a][K-1-b] * dy~[n][c][u + a - r][v + b - r]
 //                    (dy~ zero outside the image; dx = g for the zero border,
-//                    the clamp border adds the edge fold of dw_fixup.cu)
+//                    the clamp border adds the edge fold of dw_misc.cu:
+//                    dw_fold_rows_kernel / dw_fold_cols_kernel in FP32,
+//                    dw_fixup_kernel with dw_fold.cuh in BF16)
 //   dw[c][a][b]    = sum_{n,i,j} dy[n][c][i][j] * x~[n][c][i + a - r][j + b - r]
 //
 // Design (one CTA of 8 warps per 64 x 128 or 32 x 128 output tile):
 //  * The input tile and its halo are staged once into shared memory in the
-//    storage type (FP32 or BF16) with asynchronous cp.async copies; the border
-//    rule is applied while staging, so the compute loops never branch on
-//    coordinates.  BF16 is widened to FP32 when a row enters registers.  The
-//    column halo is rounded up to 4 so every staged row stays 16-byte (FP32)
-//    or 8-byte (BF16) aligned.
+//    storage type (FP32 or BF16).  When a plane's base and row stride are
+//    16-byte aligned, one thread issues a TMA tensor load per tile (the
+//    out-of-image part arrives as zeros: the zero border; under the clamp
+//    border the edge tiles are then fixed in shared memory by clamp_fix);
+//    other inputs are staged by every thread's cp.async copies with the border
+//    rule applied while copying.  Either way the compute loops never branch on
+//    coordinates.  BF16 is widened to FP32 once per staged tile (forward and
+//    fused backward) or when a row enters registers.  The column halo is
+//    rounded up to 16 bytes of elements so every staged row stays 16-byte
+//    aligned (TMA's rule for the x coordinate).
 //  * Each lane owns 4 adjacent output columns and PY rows.  The filter is
 //    consumed A rows at a time with those A rows held in registers; every
 //    staged input row is read once per group with 128-bit shared loads and

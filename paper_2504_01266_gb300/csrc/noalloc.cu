@@ -30,7 +30,10 @@ constexpr int64_t kNoAllocScratchFloats = (int64_t)(kNoAllocScratchBytes / sizeo
 static __device__ __align__(256) float g_filter_scratch[kNoAllocScratchFloats];
 
 // Device address of g_filter_scratch, looked up once per device with that
-// device current (the symbol's host-side name is not a device address).
+// device current (the symbol's host-side name is not a device address).  The
+// address is kept for the life of the process: after cudaDeviceReset the
+// module is loaded again, possibly elsewhere, so the cached address no longer
+// names the array (the header says so).
 static std::mutex g_scratch_mu;
 static void* g_scratch_ptr[64] = {};
 
@@ -95,9 +98,14 @@ extern "C" giga_status_t giga_conv2d_bwd_filter_noalloc(const giga_conv2d_desc_t
   std::memset(&a, 0, sizeof(a));
   a.N = desc->N; a.C = desc->C_in; a.H = desc->H; a.W = desc->W; a.K = desc->K;
   a.border = desc->border; a.dtype = desc->dtype;
-  // Fewest tiles per CTA (the default or more) whose partial sums fit the
-  // scratch array; a problem whose N*C*K*K partials alone exceed it is refused.
-  DwConfig cfg = tune_config(TUNE_BWD_FILTER, 0, a);
+  // The chunking giga_conv2d_bwd_filter would use (the tuner's cached or
+  // pinned choice; the built-in default if none, or with the tuner off; this
+  // entry point never benchmarks), doubled until the partial sums fit the
+  // scratch array.  A problem whose N*C*K*K partials alone exceed it is
+  // refused.
+  int id = tune_mode() == 0 ? 0 : tune_lookup(TUNE_BWD_FILTER, a);
+  if (id < 0) id = 0;
+  DwConfig cfg = tune_config(TUNE_BWD_FILTER, id, a);
   const int64_t tiles = dw_bwd_chunks_per_plane(desc->H, desc->W, 1);
   int64_t tpc = cfg.tiles_per_cta;
   while (planes * dw_bwd_chunks_per_plane(desc->H, desc->W, (int)tpc) * kk > kNoAllocScratchFloats &&

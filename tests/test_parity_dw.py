@@ -281,6 +281,52 @@ def test_plain_scale_sampled(giga, K):
     torch.cuda.empty_cache()
 
 
+# The benchmark's tuned backward for 8 x 3 x 4096 x 4096 FP32 clamp: the fused
+# kernel with 16 tiles per CTA at K = 3 (id 4) and automatic tiles per CTA at
+# K = 7 (id 0); the two-pass split at K = 15 (id 5).
+BENCH_BWD_CHOICE = {3: 4, 7: 0, 15: 5}
+
+
+@pytest.mark.parametrize("K", [3, 7, 15])
+def test_plain_scale_backward_sampled(giga, tmp_path, K):
+    """8 x 3 x 4096 x 4096 FP32, clamp border, both gradients in the
+    benchmark's tuned launch configuration: sampled dx pixels of the first and
+    last image (edge rows and columns, where the clamp fold adds the margin
+    sums, and the rows next to them included) and filter-gradient taps summed
+    over the whole batch, against the oracle."""
+    x, w = workloads.plain_scale(K)
+    dy = workloads.plain_scale_dy()
+    N, C, H, W = x.shape
+    xc, wc, dyc = x.cuda(), w.cuda(), dy.cuda()
+    with _CachedMode():
+        _force_candidates(tmp_path, (N, C, H, W), K, "clamp", torch.float32,
+                          {3: BENCH_BWD_CHOICE[K]})
+        dx, dw = giga.conv2d_bwd(xc, dyc, wc, "clamp")
+        torch.cuda.synchronize()
+    del xc
+    imgs = [0, N - 1]
+    plane = C * H * W
+    idx = torch.unique(torch.cat([
+        workloads.sample_indices(2 * plane, 3000, salt=40 + K),
+        workloads.border_indices(2, C, H, W, per_plane=2, salt=40 + K),
+        torch.tensor([p * H * W + d * W + 777 for p in range(2 * C) for d in range(1, 9)] +
+                     [p * H * W + 1234 * W + W - 1 - d for p in range(2 * C)
+                      for d in range(1, 9)])]))
+    full = torch.tensor(imgs)[idx // plane] * plane + idx % plane
+    got = dx.reshape(-1)[full.cuda()].double().cpu().numpy()
+    dy_sub = dy[imgs].numpy().astype(np.float64)
+    ref = oracle.dw_bwd_input_points(dy_sub, w.numpy(), oracle.CLAMP, idx.numpy())
+    assert normwise(got, ref) <= FP32_TOL
+    kk = K * K
+    taps = np.array([0, K - 1, kk // 2, kk - K, kk - 1, kk + 5, 2 * kk + kk // 3])
+    ref_dw = oracle.dw_bwd_filter_taps(x.numpy().astype(np.float64),
+                                       dy.numpy().astype(np.float64), K, oracle.CLAMP, taps)
+    got_dw = to_np(dw).reshape(-1)[taps]
+    assert np.abs(got_dw - ref_dw).max() <= FP32_TOL * np.abs(ref_dw).max()
+    del dx, dw, dyc
+    torch.cuda.empty_cache()
+
+
 def test_bf16_workload_sampled(giga):
     """32 x 3 x 2048 x 2048 BF16 images, 9 x 9 filters, zero border -- the BF16
     comparison of the benchmark, in its launch configuration: sampled y and dx

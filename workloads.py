@@ -82,6 +82,12 @@ def plain_scale(K: int, N: int = 8, C: int = 3, H: int = 4096, W: int = 4096,
     return x, w
 
 
+def plain_scale_dy(N: int = 8, C: int = 3, H: int = 4096, W: int = 4096, device: str = "cpu"):
+    """Upstream gradient of the plain_scale images: normal(0, 1), (N, C, H, W)."""
+    g = generator("plain_scale", salt=100, device=device)
+    return normal((N, C, H, W), 1.0, g, device)
+
+
 def train(N: int = 16, C: int = 3, H: int = 2048, W: int = 2048, K: int = 7,
           device: str = "cpu"):
     """x uniform [0, 1), w normal(0, 0.1), dy normal(0, 1)."""
