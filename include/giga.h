@@ -317,13 +317,15 @@ giga_status_t giga_gray_conv2d_fwd(const giga_conv2d_desc_t* desc, const void* x
                                    void* y, void* stream);
 
 /* ------------------------------------------------------------------------
- * Autotuner.  Candidates: forward and input gradient (op 1 / 2): id 0..3 =
+ * Autotuner.  Candidates: forward and input gradient (op 1 / 2): id 0..7 =
  * {8, 4} rows per thread (bit 0) x {one tile per CTA, persistent
- * double-buffered CTAs} (bit 1); filter gradient (op 4): id 0..4 = tiles
+ * double-buffered CTAs} (bit 1) x {no prefetch, an L2 prefetch of the tile
+ * the CTA (or its successor) loads later} (bit 2); filter gradient (op 4): id 0..4 = tiles
  * per chunk of the persistent filter kernel {auto, 2, 4, 8, 16}; fused
  * backward (op 6): id 0..4 = the fused kernel with tiles per CTA {auto, 2,
- * 4, 8, 16}, id 5 = two passes (input gradient by the forward-style kernel,
- * filter gradient by the filter kernel).  The built-in default is id 0.
+ * 4, 8, 16}, id 5 = two passes (input gradient by the forward-style kernel
+ * in the forward's tuned configuration, filter gradient by the filter
+ * kernel).  The built-in default is id 0.
  * Modes (also from the environment variable GIGA_AUTOTUNE=off|cached|full):
  *   0 off:    always the built-in default configuration;
  *   1 cached: use a cached choice when one exists (default);

@@ -228,7 +228,10 @@ giga_status_t run_dw_op(int op, const DwArgs& a, const DwConfig& cfg, cudaStream
         // input gradient by the forward-style kernel, filter gradient by the
         // persistent filter kernel: two passes over dy, each role on its own
         // best kernel (faster for the ALU-bound large filters)
-        DwConfig fc = tune_config(TUNE_FWD, 0, a);
+        // the input-gradient pass runs the forward kernel on a problem of the
+        // same shape: take the forward's tuned configuration
+        int fid = tune_mode() == 0 ? 0 : tune_lookup(TUNE_FWD, a);
+        DwConfig fc = tune_config(TUNE_FWD, fid < 0 ? 0 : fid, a);
         giga_status_t s2 = run_dw_op(TUNE_BWD_INPUT, a, fc, st);
         if (s2 != GIGA_OK) return s2;
         return run_dw_op(TUNE_BWD_FILTER, a, cfg, st);

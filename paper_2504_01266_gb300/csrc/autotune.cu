@@ -4,7 +4,9 @@
 //
 // Candidates:
 //   forward / input gradient: output rows per thread 8 (64 x 128 tiles) or
-//                             4 (32 x 128 tiles: twice the CTAs, less halo reuse);
+//                             4 (32 x 128 tiles: twice the CTAs, less halo reuse)
+//                             x one tile per CTA or persistent CTAs x with or
+//                             without an L2 prefetch of a later tile;
 //   filter gradient (alone or fused): tiles per CTA = automatic, 2, 4, 8, 16
 //                             (fewer partial sums vs. better load balance).
 // Problem class: (op, dtype, K, border, floor(log2(N*C*H*W))).
@@ -45,13 +47,13 @@ int tune_mode() {
 }
 
 // Forward / input gradient: {8, 4} rows per thread x {one tile per CTA,
-// persistent}; filter gradient: tiles per chunk {auto, 2, 4, 8, 16}; fused
+// persistent} x {no prefetch, L2 prefetch}; filter gradient: tiles per chunk {auto, 2, 4, 8, 16}; fused
 // backward: the fused kernel with tiles per CTA {auto, 2, 4, 8, 16}, or the
 // two-pass split.
 int tune_candidates(int op) {
   switch (op) {
     case TUNE_FWD:
-    case TUNE_BWD_INPUT: return 4;
+    case TUNE_BWD_INPUT: return 8;
     case TUNE_BWD_FILTER: return 5;
     default: return 6;
   }
@@ -92,6 +94,7 @@ DwConfig tune_config(int op, int id, const DwArgs& a) {
   DwConfig c;
   c.rows_per_thread = 8;
   c.persistent = 0;
+  c.prefetch = 0;
   c.split = 0;
   c.tiles_per_cta = op == TUNE_BWD_FILTER ? auto_filter_tiles_per_chunk(a) : auto_tiles_per_cta(a);
   static const int tpc[5] = {0, 2, 4, 8, 16};
@@ -100,6 +103,7 @@ DwConfig tune_config(int op, int id, const DwArgs& a) {
     case TUNE_BWD_INPUT:
       c.rows_per_thread = (id & 1) ? 4 : 8;
       c.persistent = (id & 2) ? 1 : 0;
+      c.prefetch = (id & 4) ? 1 : 0;
       break;
     case TUNE_BWD_FILTER:
       if (id >= 1 && id <= 4) c.tiles_per_cta = tpc[id];

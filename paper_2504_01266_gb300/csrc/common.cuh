@@ -64,6 +64,7 @@ struct DwArgs {
 struct DwConfig {
   int rows_per_thread;  // forward / input-gradient kernel: 4 or 8
   int persistent;       // forward / input-gradient kernel: 1 = persistent, double-buffered
+  int prefetch;         // forward / input-gradient kernel: 1 = L2 prefetch of a later tile
   int tiles_per_cta;    // filter-gradient kernels: consecutive tiles per chunk
   int split;            // fused backward: 1 = input and filter gradients as two passes
 };

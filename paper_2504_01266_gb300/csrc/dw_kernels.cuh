@@ -633,7 +633,7 @@ template <typename T, int K, int PY>
 __device__ __forceinline__ void dw_fwd_body(
     const CUtensorMap& tmx, const T* __restrict__ x, const float* __restrict__ w,
     T* __restrict__ y, FastDiv fc, int H, int W, FastDiv ftx, FastDiv fty, int64_t num_tiles,
-    int clamp, int vec, int flip, int use_tma, int* err) {
+    int clamp, int vec, int flip, int use_tma, int64_t pf, int* err) {
   using G = Geo<K>;
   using GS = Geo<K, sizeof(T)>;
   using S = FwdShape<K, PY, T>;
@@ -688,6 +688,13 @@ __device__ __forceinline__ void dw_fwd_body(
   uint32_t phase = 0;  // bit s: parity of the next TMA completion on stage s
   int sb = 0;
   for (; t < num_tiles; t += gridDim.x, sb ^= 1) {
+    // L2 prefetch of the tile this CTA's successor (one tile per CTA) or this
+    // CTA two tiles on (persistent) will load: its TMA load then hits L2
+    if (use_tma && pf > 0 && threadIdx.x == 0 && t + pf < num_tiles) {
+      int py0, px0, pplane;
+      coords(t + pf, py0, px0, pplane);
+      tma_prefetch_3d(&tmx, px0 - GS::RP, py0 - G::R, pplane);
+    }
     const int64_t tn = t + gridDim.x;
     if (tn < num_tiles) {
       stage(tn, sb ^ 1);  // the other stage was released by the barrier below
@@ -731,9 +738,9 @@ template <typename T, int K, int PY>
 __global__ void __launch_bounds__(kThreads) dw_fwd_kernel(
     const __grid_constant__ CUtensorMap tmx, const T* __restrict__ x, const float* __restrict__ w,
     T* __restrict__ y, FastDiv fc, int H, int W, FastDiv ftx, FastDiv fty, int64_t num_tiles,
-    int clamp, int vec, int flip, int use_tma, int* err) {
+    int clamp, int vec, int flip, int use_tma, int64_t pf, int* err) {
   dw_fwd_body<T, K, PY>(tmx, x, w, y, fc, H, W, ftx, fty, num_tiles, clamp, vec, flip, use_tma,
-                        err);
+                        pf, err);
 }
 
 // The same pass compiled for five CTAs per SM (at most 51 registers).  Used
@@ -745,9 +752,9 @@ template <typename T, int K, int PY>
 __global__ void __launch_bounds__(kThreads, 5) dw_fwd_kernel_hi_occ(
     const __grid_constant__ CUtensorMap tmx, const T* __restrict__ x, const float* __restrict__ w,
     T* __restrict__ y, FastDiv fc, int H, int W, FastDiv ftx, FastDiv fty, int64_t num_tiles,
-    int clamp, int vec, int flip, int use_tma, int* err) {
+    int clamp, int vec, int flip, int use_tma, int64_t pf, int* err) {
   dw_fwd_body<T, K, PY>(tmx, x, w, y, fc, H, W, ftx, fty, num_tiles, clamp, vec, flip, use_tma,
-                        err);
+                        pf, err);
 }
 
 // ------------------------------------------------------ separable filter

@@ -31,7 +31,8 @@ static cudaError_t fwd_kernel_for(bool persistent, size_t smem,
 }
 
 template <typename T, int K, int PY>
-static cudaError_t fwd_impl(const DwArgs& a, bool input_grad, bool persistent, cudaStream_t st) {
+static cudaError_t fwd_impl(const DwArgs& a, bool input_grad, bool persistent, bool prefetch,
+                            cudaStream_t st) {
   using S = FwdShape<K, PY, T>;
   decltype(&dw_fwd_kernel<T, K, PY>) kern = nullptr;
   cudaError_t e = fwd_kernel_for<T, K, PY>(persistent, (size_t)S::SM_BYTES, &kern);
@@ -40,23 +41,28 @@ static cudaError_t fwd_impl(const DwArgs& a, bool input_grad, bool persistent, c
   const int64_t tiles_y = (a.H + S::TH - 1) / S::TH;
   const int64_t tiles = a.N * a.C * tiles_x * tiles_y;
   int64_t grid = tiles;
-  size_t smem = (size_t)S::SM_BYTES_1;
-  if (persistent) {
-    smem = (size_t)S::SM_BYTES;
-    static int ctas_per_sm[64] = {};
-    int dev = 0;
-    cudaGetDevice(&dev);
-    int& per_sm = ctas_per_sm[dev & 63];
-    if (per_sm == 0) {
-      int v = 0;
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kern, kThreads, smem) !=
-              cudaSuccess ||
-          v < 1)
-        v = 1;
-      per_sm = v;
-    }
-    grid = std::min<int64_t>(tiles, (int64_t)per_sm * sm_count());
+  const size_t smem = persistent ? (size_t)S::SM_BYTES : (size_t)S::SM_BYTES_1;
+  // resident CTAs per SM of this compilation at this shared-memory size
+  // (per device, per persistence mode)
+  static int ctas_per_sm[64][2] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int& per_sm = ctas_per_sm[dev & 63][persistent ? 1 : 0];
+  if (per_sm == 0) {
+    int v = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kern, kThreads, smem) != cudaSuccess ||
+        v < 1)
+      v = 1;
+    per_sm = v;
   }
+  const int64_t resident = (int64_t)per_sm * sm_count();
+  if (persistent) grid = std::min<int64_t>(tiles, resident);
+  // L2 prefetch distance in tiles (0: none): one tile per CTA -- the tile of
+  // the CTA that starts when this one ends (one wave of resident CTAs
+  // later); persistent -- this CTA's tile after next (the next is being
+  // loaded).  A tuning option: it helps where the tile load's latency shows
+  // (FP32 K = 7, 9) and costs where HBM is already saturated (K = 3).
+  const int64_t pf = !prefetch ? 0 : persistent ? 2 * grid : resident;
   if (tiles > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
   const T* in = static_cast<const T*>(input_grad ? a.dy : a.x);
   T* out = static_cast<T*>(input_grad ? a.dx : a.y);
@@ -70,7 +76,7 @@ static cudaError_t fwd_impl(const DwArgs& a, bool input_grad, bool persistent, c
   kern<<<(unsigned)grid, kThreads, smem, st>>>(
       tm, in, a.w, out, make_fastdiv((uint32_t)a.C), (int)a.H, (int)a.W,
       make_fastdiv((uint32_t)tiles_x), make_fastdiv((uint32_t)tiles_y), tiles,
-      input_grad ? 0 : a.border, a.vec, input_grad ? 1 : 0, use_tma, dw_error_word());
+      input_grad ? 0 : a.border, a.vec, input_grad ? 1 : 0, use_tma, pf, dw_error_word());
   note_launch();
   return cudaGetLastError();
 }
@@ -79,12 +85,12 @@ template <int K>
 cudaError_t dw_fwd_launch(const DwArgs& a, const DwConfig& cfg, bool input_grad,
                           cudaStream_t st) {
   const bool py4 = cfg.rows_per_thread == 4;
-  const bool pers = cfg.persistent != 0;
+  const bool pers = cfg.persistent != 0, pf = cfg.prefetch != 0;
   if (a.dtype == 0)
-    return py4 ? fwd_impl<float, K, 4>(a, input_grad, pers, st)
-               : fwd_impl<float, K, 8>(a, input_grad, pers, st);
-  return py4 ? fwd_impl<__nv_bfloat16, K, 4>(a, input_grad, pers, st)
-             : fwd_impl<__nv_bfloat16, K, 8>(a, input_grad, pers, st);
+    return py4 ? fwd_impl<float, K, 4>(a, input_grad, pers, pf, st)
+               : fwd_impl<float, K, 8>(a, input_grad, pers, pf, st);
+  return py4 ? fwd_impl<__nv_bfloat16, K, 4>(a, input_grad, pers, pf, st)
+             : fwd_impl<__nv_bfloat16, K, 8>(a, input_grad, pers, pf, st);
 }
 
 template <typename T, int K>

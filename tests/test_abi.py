@@ -135,7 +135,8 @@ def test_autotune_set_choice(lib):
         assert _lib.giga_autotune_set_choice(d, fused, 5) == _lib.GIGA_OK
         assert _lib.giga_autotune_choice(d, fused) == 5
         assert _lib.giga_autotune_choice(d, _lib.GIGA_OP_FWD) == 0  # other ops untouched
-        assert _lib.giga_autotune_set_choice(d, _lib.GIGA_OP_FWD, 4) == _lib.GIGA_ERR_INVALID_ARG
+        assert _lib.giga_autotune_set_choice(d, _lib.GIGA_OP_FWD, 7) == _lib.GIGA_OK
+        assert _lib.giga_autotune_set_choice(d, _lib.GIGA_OP_FWD, 8) == _lib.GIGA_ERR_INVALID_ARG
         assert _lib.giga_autotune_set_choice(d, _lib.GIGA_OP_BWD_FILTER, 5) == \
             _lib.GIGA_ERR_INVALID_ARG
         assert _lib.giga_autotune_set_choice(d, 3, 0) == _lib.GIGA_ERR_INVALID_ARG

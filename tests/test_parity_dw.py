@@ -181,7 +181,8 @@ class _CachedMode:
     (15, "clamp", torch.bfloat16, 1000)])
 def test_fwd_every_configuration(giga, tmp_path, K, border, dtype, W):
     """Every forward / input-gradient configuration ({8, 4} rows per thread x
-    one tile per CTA or persistent double-buffered CTAs) on planes holding
+    one tile per CTA or persistent double-buffered CTAs x with or without the
+    L2 prefetch of a later tile) on planes holding
     more tiles than a persistent grid has CTAs, so each persistent CTA runs
     two or three tiles through its two shared-memory stages and the last
     round is ragged.  FP32 with W = 1000 is staged by TMA (the clamp border's
@@ -196,7 +197,7 @@ def test_fwd_every_configuration(giga, tmp_path, K, border, dtype, W):
         mag_y = oracle.dw_fwd(np.abs(xr), np.abs(wn), b)
         mag_dx = oracle.dw_bwd_input(np.abs(dyr), np.abs(wn), b)
     with _CachedMode():
-        for cand in range(4):
+        for cand in range(8):
             _force_candidates(tmp_path, shape, K, border, dtype, {0: cand, 1: cand})
             y = poison_like(xc)
             giga.conv2d_fwd(xc, wc, border, out=y)
