@@ -781,7 +781,7 @@ template <typename T, int K>
 __global__ void __launch_bounds__(kThreads) dw_sep_kernel(
     const __grid_constant__ CUtensorMap tmx, const T* __restrict__ x,
     const float* __restrict__ wcol, const float* __restrict__ wrow, T* __restrict__ y, FastDiv fc,
-    int H, int W, FastDiv ftx, FastDiv fty, int clamp, int vec, int use_tma, int* err) {
+    int H, int W, FastDiv ftx, FastDiv fty, int clamp, int vec, int use_tma, int pf, int* err) {
   using G = Geo<K>;
   using GS = Geo<K, sizeof(T)>;
   using S = SepShape<K, T>;
@@ -821,6 +821,13 @@ __global__ void __launch_bounds__(kThreads) dw_sep_kernel(
       fence_proxy_async();
       mbar_expect_tx(bar, (uint32_t)ST::STAGE_BYTES);
       tma_load_3d(staged, &tmx, tx0 - GS::RP, ty0 - G::R, plane, bar);
+      // L2 prefetch of the tile the CTA starting one wave of resident CTAs
+      // later will load
+      if (pf > 0 && t + (uint32_t)pf < gridDim.x) {
+        const uint32_t u = t + (uint32_t)pf, u2 = fdiv(u, ftx), upl = fdiv(u2, fty);
+        tma_prefetch_3d(&tmx, (int)(u - u2 * ftx.d) * kTileW - GS::RP,
+                        (int)(u2 - upl * fty.d) * S::TH - G::R, (int)upl);
+      }
     }
     cp_async_wait_all();
     if (!mbar_wait(bar, 0)) {
