@@ -333,7 +333,9 @@ giga_status_t giga_gray_conv2d_fwd(const giga_conv2d_desc_t* desc, const void* x
  *             first time they meet an uncached problem class (not while the
  *             stream is capturing).
  * The cache is kept in memory and, if GIGA_AUTOTUNE_CACHE names a file,
- * loaded from / saved to it as JSON.  A corrupt cache file is ignored. */
+ * loaded from / saved to it as JSON.  A corrupt cache file is ignored.  With
+ * GIGA_LOG set (to anything but "0") every tuning decision, including the
+ * ragged plan's, is printed to standard error with each candidate's time. */
 giga_status_t giga_autotune_set_mode(int32_t mode);
 int32_t giga_autotune_get_mode(void);
 /* Benchmark every candidate for this problem on the given buffers (outputs

@@ -205,6 +205,22 @@ void tune_store(int op, const DwArgs& a, int id) {
   if (const char* p = std::getenv("GIGA_AUTOTUNE_CACHE")) save_file(p);
 }
 
+// GIGA_LOG=1 (or any value but 0): each tuning decision is printed to
+// standard error, one line per (op, problem class) with every candidate's time.
+bool tune_log_enabled() {
+  const char* e = std::getenv("GIGA_LOG");
+  return e && *e && std::strcmp(e, "0") != 0;
+}
+
+static const char* op_name(int op) {
+  switch (op) {
+    case TUNE_FWD: return "forward";
+    case TUNE_BWD_INPUT: return "input-gradient";
+    case TUNE_BWD_FILTER: return "filter-gradient";
+    default: return "fused-backward";
+  }
+}
+
 giga_status_t tune_dw_op(int op, const DwArgs& a, cudaStream_t st) {
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess) return fail(GIGA_ERR_CUDA, "event create");
@@ -214,6 +230,7 @@ giga_status_t tune_dw_op(int op, const DwArgs& a, cudaStream_t st) {
   }
   int best = 0;
   float best_ms = 1e30f;
+  std::string times;
   giga_status_t status = GIGA_OK;
   for (int id = 0; id < tune_candidates(op) && status == GIGA_OK; ++id) {
     const DwConfig cfg = tune_config(op, id, a);
@@ -229,6 +246,9 @@ giga_status_t tune_dw_op(int op, const DwArgs& a, cudaStream_t st) {
     }
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
+    char buf[48];
+    std::snprintf(buf, sizeof(buf), "%s%d:%.3f", id ? " " : "", id, ms / 3.f);
+    times += buf;
     if (ms < best_ms) {
       best_ms = ms;
       best = id;
@@ -236,7 +256,16 @@ giga_status_t tune_dw_op(int op, const DwArgs& a, cudaStream_t st) {
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if (status == GIGA_OK) tune_store(op, a, best);
+  if (status == GIGA_OK) {
+    tune_store(op, a, best);
+    if (tune_log_enabled())
+      std::fprintf(stderr,
+                   "giga autotune: %s %s K=%d %s N*C*H*W=%lld (class %s) -> candidate %d "
+                   "(ms per call: %s)\n",
+                   op_name(op), a.dtype ? "bf16" : "f32", a.K, a.border ? "clamp" : "zero",
+                   (long long)(a.N * a.C * a.H * a.W), key_of(op, a).c_str(), best,
+                   times.c_str());
+  }
   return status;
 }
 

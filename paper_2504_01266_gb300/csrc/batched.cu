@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdio>
 #include <cstring>
 #include <new>
 #include <numeric>
@@ -349,6 +350,7 @@ giga_status_t giga_batched_plan_autotune(giga_batched_plan_t plan, void* ws, siz
   float best_ms = 0.f;
   const int prev = plan->tpc;
   int best = prev;
+  std::string times;
   for (int tpc : kRagTpcCandidates) {
     if ((s = build_plan(im, n, plan->ops, plan->border, plan->dtype, false, tpc, plan)) != GIGA_OK)
       break;
@@ -364,6 +366,9 @@ giga_status_t giga_batched_plan_autotune(giga_batched_plan_t plan, void* ws, siz
       s = cuda_fail(e, "autotune timing");
       break;
     }
+    char buf[48];
+    std::snprintf(buf, sizeof(buf), "%s%d:%.3f ms", times.empty() ? "" : " ", tpc, ms / 3.f);
+    times += buf;
     if (tpc == kRagTpcCandidates[0] || ms < best_ms) {
       best_ms = ms;
       best = tpc;
@@ -383,6 +388,9 @@ giga_status_t giga_batched_plan_autotune(giga_batched_plan_t plan, void* ws, siz
     return s;
   if ((s = giga_batched_plan_upload(plan, ws, ws_bytes, stream)) != GIGA_OK) return s;
   if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "autotune sync");
+  if (tune_log_enabled())
+    std::fprintf(stderr, "giga autotune: ragged batch of %d images -> %d tiles per chunk (%s)\n",
+                 n, best, times.c_str());
   if (tiles_per_chunk) *tiles_per_chunk = best;
   return GIGA_OK;
 }

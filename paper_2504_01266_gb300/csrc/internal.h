@@ -27,6 +27,8 @@ void tune_store(int op, const DwArgs& a, int id);
 giga_status_t run_dw_op(int op, const DwArgs& a, const DwConfig& cfg, cudaStream_t st);
 // Benchmark all candidates of `op` on these buffers and store the fastest.
 giga_status_t tune_dw_op(int op, const DwArgs& a, cudaStream_t st);
+// GIGA_LOG is set (to anything but "0"): tuning decisions go to standard error.
+bool tune_log_enabled();
 
 // Dense 3 x 3, 64 -> 64 channel path (dense.cu).
 size_t dense_workspace_bytes(bool input_grad);

@@ -4,6 +4,7 @@ the on-demand tuning of mode 2): every op is benchmarked on a problem of
 recorded choice is a valid candidate, the entry points then run with it and
 match the FP64 oracle, and a saved cache reloads to the same choices."""
 import json
+import os
 
 import numpy as np
 import pytest
@@ -119,3 +120,31 @@ def test_mode_full_tunes_an_uncached_problem_on_first_use(giga, tmp_path):
         xr, wn = x.double().numpy(), w.numpy()
         assert_fp32(to_np(y), oracle.dw_fwd(xr, wn, oracle.ZERO),
                     oracle.dw_fwd(np.abs(xr), np.abs(wn), oracle.ZERO), K * K, "fwd")
+
+
+def test_giga_log_prints_tuning_decisions(giga, capfd):
+    """GIGA_LOG=1: every tuning decision is printed to standard error with
+    the time of each candidate."""
+    from paper_2504_01266_gb300 import _lib as L
+    x, w, dy = _data(3, 960)
+    xc, wc = x.cuda(), w.cuda()
+    N, C, H, W = SHAPE
+    d = L.desc(N, C, C, H, W, 3, C, 0, L.GIGA_F32, L.GIGA_LAYOUT_NCHW)
+    y = torch.empty_like(xc)
+    old = os.environ.get("GIGA_LOG")
+    os.environ["GIGA_LOG"] = "1"
+    try:
+        with _Mode(1):
+            capfd.readouterr()
+            L.check(L.giga_autotune_conv2d(d, 1, xc.data_ptr(), wc.data_ptr(), y.data_ptr(),
+                                           0, 0, 0, 0, 0, torch.cuda.current_stream().cuda_stream),
+                    "autotune")
+            err = capfd.readouterr().err
+    finally:
+        if old is None:
+            del os.environ["GIGA_LOG"]
+        else:
+            os.environ["GIGA_LOG"] = old
+    line = [ln for ln in err.splitlines() if ln.startswith("giga autotune: forward f32 K=3 zero")]
+    assert len(line) == 1, err
+    assert "candidate" in line[0] and line[0].count(":") >= 8 + 1
