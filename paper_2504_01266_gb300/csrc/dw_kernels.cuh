@@ -193,6 +193,25 @@ __device__ __forceinline__ float4 load_chunk(const T* __restrict__ plane, int H,
   return v;
 }
 
+// Four consecutive FP32 elements inside an image row whose start is not
+// 16-byte aligned (W not a multiple of 4, or a view): the widest copies the
+// source address allows -- one 16-byte copy on the rows that happen to be
+// aligned, two 8-byte copies on 8-byte boundaries (every row when W = 2 mod 4,
+// half of them when W is odd), else four 4-byte copies.  `dst` is 16-byte
+// aligned.
+__device__ __forceinline__ void stage_chunk_unaligned(float* dst, const float* src) {
+  const uintptr_t a = reinterpret_cast<uintptr_t>(src);
+  if ((a & 15) == 0) {
+    cp_async16(dst, src, true);
+  } else if ((a & 7) == 0) {
+    cp_async8(dst, src, true);
+    cp_async8(dst + 2, src + 2, true);
+  } else {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) cp_async4(dst + q, src + q, true);
+  }
+}
+
 // Stage rows [ty0 - HR, ty0 - HR + rows) x cols [tx0 - HC, tx0 - HC + pitch)
 // of one image plane into shared memory (same element type as the tensor).
 // Outside the image: zero, or (clamp) the nearest edge pixel, row and column
@@ -226,6 +245,8 @@ __device__ __forceinline__ void stage_tile(T* __restrict__ sm, const T* __restri
       const T* src = plane + (int64_t)gi * W;
       if (vec && gj >= 0 && gj + 3 < W) {
         cp_async16(reinterpret_cast<float*>(dst), src + gj, true);
+      } else if (gj >= 0 && gj + 3 < W) {
+        stage_chunk_unaligned(reinterpret_cast<float*>(dst), src + gj);
       } else {
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -246,6 +267,12 @@ __device__ __forceinline__ void stage_tile(T* __restrict__ sm, const T* __restri
       const T* src = plane + (int64_t)gi * W;
       if (vec && gj >= 0 && gj + 3 < W) {
         cp_async8(dst, src + gj, true);
+      } else if (gj >= 0 && gj + 3 < W &&
+                 (reinterpret_cast<uintptr_t>(src + gj) & 3) == 0) {
+        // interior chunk of a row that is not 8-byte aligned, at a 4-byte
+        // boundary: two 4-byte copies of two elements each
+        cp_async4(reinterpret_cast<float*>(dst), src + gj, true);
+        cp_async4(reinterpret_cast<float*>(dst) + 1, src + gj + 2, true);
       } else {
         Tile<T>::store4(dst, load_chunk<T>(plane, H, W, gi, gj, clamp, vec));
       }
@@ -281,6 +308,8 @@ __device__ __forceinline__ void stage_tile_rt(T* __restrict__ sm, const T* __res
       const T* src = plane + (int64_t)gi * W;
       if (vec && gj >= 0 && gj + 3 < W) {
         cp_async16(reinterpret_cast<float*>(dst), src + gj, true);
+      } else if (gj >= 0 && gj + 3 < W) {
+        stage_chunk_unaligned(reinterpret_cast<float*>(dst), src + gj);
       } else {
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -301,6 +330,12 @@ __device__ __forceinline__ void stage_tile_rt(T* __restrict__ sm, const T* __res
       const T* src = plane + (int64_t)gi * W;
       if (vec && gj >= 0 && gj + 3 < W) {
         cp_async8(dst, src + gj, true);
+      } else if (gj >= 0 && gj + 3 < W &&
+                 (reinterpret_cast<uintptr_t>(src + gj) & 3) == 0) {
+        // interior chunk of a row that is not 8-byte aligned, at a 4-byte
+        // boundary: two 4-byte copies of two elements each
+        cp_async4(reinterpret_cast<float*>(dst), src + gj, true);
+        cp_async4(reinterpret_cast<float*>(dst) + 1, src + gj + 2, true);
       } else {
         Tile<T>::store4(dst, load_chunk<T>(plane, H, W, gi, gj, clamp, vec));
       }
