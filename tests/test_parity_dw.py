@@ -262,6 +262,36 @@ def test_bwd_every_configuration(giga, tmp_path, K, border, dtype, W):
             check_dw(dw, (K, border, dtype, "fused", cand))
 
 
+# Shapes at the edges of the tiling: one image row of 2^20 pixels (TMA
+# staging: 8,192 tile columns), the same with W % 4 = 3 (cp.async staging of
+# unaligned rows), 2^20 + 1 rows of 3 pixels (16,385 tile rows of one
+# partial column), and 65,537 planes of 4 x 4 (as many CTAs and filter
+# channels, every tile mostly halo).
+EXTREME = [((1, 1, 3, 1 << 20), 5), ((1, 1, 5, (1 << 20) + 3), 3),
+           ((1, 1, (1 << 20) + 1, 3), 3), ((1, 65537, 4, 4), 3)]
+
+
+@pytest.mark.parametrize("shape,K", EXTREME)
+@pytest.mark.parametrize("border", ["zero", "clamp"])
+def test_extreme_shapes(giga, shape, K, border):
+    x, w, dy = make(shape, K, 1000 + K + shape[1] % 7)
+    xc, wc, dyc = x.cuda(), w.cuda(), dy.cuda()
+    b = BORDER[border]
+    y = giga.conv2d_fwd(xc, wc, border, out=poison_like(xc))
+    dx, dw = giga.conv2d_bwd(xc, dyc, wc, border, dx=poison_like(dyc),
+                             dw=torch.full((shape[1], K, K), float("nan"), device="cuda"))
+    torch.cuda.synchronize()
+    xr, dyr, wn = x.double().numpy(), dy.double().numpy(), w.numpy()
+    ax, ady, aw = np.abs(xr), np.abs(dyr), np.abs(wn)
+    what = (shape, K, border)
+    assert_fp32(to_np(y), oracle.dw_fwd(xr, wn, b), oracle.dw_fwd(ax, aw, b), K * K, what)
+    assert_fp32(to_np(dx), oracle.dw_bwd_input(dyr, wn, b), oracle.dw_bwd_input(ady, aw, b),
+                (K // 2 + 1) ** 2 * K * K, what)
+    n = shape[0] * shape[2] * shape[3]
+    assert_fp32(to_np(dw), oracle.dw_bwd_filter(xr, dyr, K, b),
+                oracle.dw_bwd_filter(ax, ady, K, b), n, what)
+
+
 # ------------------------------------------------------- full-size workloads
 
 @pytest.mark.parametrize("K", [3, 7, 15])
