@@ -988,8 +988,9 @@ def run_giga(args):
         f, b = by[(K, "fwd")], by[(K, "bwd")]
         kernels.append((f["ms"] * (2 if split else 1), f"dw_fwd_kernel<float,{K},8>", f))
         if not split:
-            kernels.append((b["ms"], f"dw_bwd_kernel<float,{K}> (with its fold/finalize "
-                                     "launches)", b))
+            ring = tuned.get(K, {}).get("bwd") == 6
+            kernels.append((b["ms"], f"dw_bwd{'_ring' if ring else ''}_kernel<float,{K}> (with "
+                                     "its fold/finalize launches)", b))
         else:
             kernels.append((b["ms"] - f["ms"], f"dw_filter_kernel<float,{K}>", None))
     _, kname, dom = max((k for k in kernels if k[2] is not None), key=lambda k: k[0])
@@ -1185,7 +1186,8 @@ def main():
     ap.add_argument("--no-tune", action="store_true", help="built-in default configurations")
     ap.add_argument("--pin-bwd", type=int, default=None,
                     help="backward configuration id for every K instead of tuning it "
-                         "(0-4: fused kernel, tiles per CTA auto/2/4/8/16; 5: two passes)")
+                         "(0-4: fused kernel, tiles per CTA auto/2/4/8/16; 5: two passes; "
+                         "6: persistent kernel with a two-stage tile ring)")
     ap.add_argument("--tune-cache", default="",
                     help="autotune cache file: load it and skip tuning if it exists, "
                          "else tune and save the choices there")

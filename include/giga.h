@@ -325,7 +325,8 @@ giga_status_t giga_gray_conv2d_fwd(const giga_conv2d_desc_t* desc, const void* x
  * backward (op 6): id 0..4 = the fused kernel with tiles per CTA {auto, 2,
  * 4, 8, 16}, id 5 = two passes (input gradient by the forward-style kernel
  * in the forward's tuned configuration, filter gradient by the filter
- * kernel).  The built-in default is id 0.
+ * kernel), id 6 = one persistent kernel whose CTAs stream (x, dy) tile pairs
+ * through a two-stage ring (the HBM-bound small filters).  The built-in default is id 0.
  * Modes (also from the environment variable GIGA_AUTOTUNE=off|cached|full):
  *   0 off:    always the built-in default configuration;
  *   1 cached: use a cached choice when one exists (default);

@@ -236,7 +236,12 @@ giga_status_t run_dw_op(int op, const DwArgs& a, const DwConfig& cfg, cudaStream
         if (s2 != GIGA_OK) return s2;
         return run_dw_op(TUNE_BWD_FILTER, a, cfg, st);
       }
-      e = dispatch_k_filter(a.K, [&](auto k) { return dw_bwd_launch<decltype(k)::value>(a, cfg, st); });
+      if (cfg.ring)
+        e = dispatch_k_filter(a.K, [&](auto k) {
+          return dw_bwd_ring_launch<decltype(k)::value>(a, cfg, st);
+        });
+      else
+        e = dispatch_k_filter(a.K, [&](auto k) { return dw_bwd_launch<decltype(k)::value>(a, cfg, st); });
       if (e == cudaSuccess) e = dw_fixup_launch(a, st);
       if (e == cudaSuccess)
         e = dw_finalize_launch(a, dw_bwd_chunks_per_plane(a.H, a.W, cfg.tiles_per_cta), st);

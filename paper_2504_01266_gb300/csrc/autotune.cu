@@ -48,14 +48,14 @@ int tune_mode() {
 
 // Forward / input gradient: {8, 4} rows per thread x {one tile per CTA,
 // persistent} x {no prefetch, L2 prefetch}; filter gradient: tiles per chunk {auto, 2, 4, 8, 16}; fused
-// backward: the fused kernel with tiles per CTA {auto, 2, 4, 8, 16}, or the
-// two-pass split.
+// backward: the fused kernel with tiles per CTA {auto, 2, 4, 8, 16}, the
+// two-pass split, or the persistent kernel with a two-stage tile ring.
 int tune_candidates(int op) {
   switch (op) {
     case TUNE_FWD:
     case TUNE_BWD_INPUT: return 8;
     case TUNE_BWD_FILTER: return 5;
-    default: return 6;
+    default: return 7;
   }
 }
 
@@ -96,6 +96,7 @@ DwConfig tune_config(int op, int id, const DwArgs& a) {
   c.persistent = 0;
   c.prefetch = 0;
   c.split = 0;
+  c.ring = 0;
   c.tiles_per_cta = op == TUNE_BWD_FILTER ? auto_filter_tiles_per_chunk(a) : auto_tiles_per_cta(a);
   static const int tpc[5] = {0, 2, 4, 8, 16};
   switch (op) {
@@ -110,8 +111,9 @@ DwConfig tune_config(int op, int id, const DwArgs& a) {
       break;
     default:
       if (id >= 1 && id <= 4) c.tiles_per_cta = tpc[id];
-      if (id == 5) {
-        c.split = 1;
+      if (id == 5 || id == 6) {
+        c.split = id == 5;
+        c.ring = id == 6;
         c.tiles_per_cta = auto_filter_tiles_per_chunk(a);
       }
       break;

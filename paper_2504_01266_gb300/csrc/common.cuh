@@ -67,6 +67,7 @@ struct DwConfig {
   int prefetch;         // forward / input-gradient kernel: 1 = L2 prefetch of a later tile
   int tiles_per_cta;    // filter-gradient kernels: consecutive tiles per chunk
   int split;            // fused backward: 1 = input and filter gradients as two passes
+  int ring;             // fused backward: 1 = persistent kernel with a two-stage tile ring
 };
 
 // Element access for the two storage types; arithmetic is always FP32.

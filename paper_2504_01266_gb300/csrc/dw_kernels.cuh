@@ -1336,4 +1336,223 @@ __global__ void __launch_bounds__(FilterShape<K, T>::NT, 1)
     if (pending & (1u << s)) mbar_wait(bars + s, (phase >> s) & 1u);
 }
 
+// ------------------------------------------- backward with a staging ring
+// Both gradients from one staged (x, dy) pair of halo tiles, like
+// dw_bwd_kernel (warps 0-3: the input gradient g, warps 4-7: the filter
+// gradient), but persistent over chunks of `tpc` consecutive tiles (chunk q
+// runs on CTA q mod gridDim.x, the layout of dw_filter_kernel, so the same
+// FP64 finalisation applies) with NS shared-memory stages: the copies of the
+// tile NS - 1 items ahead are in flight while the current one is computed,
+// across chunk boundaries too.  One CTA per SM.  It suits the HBM-bound small
+// filters, whose single-stage fused kernel leaves its tile loads exposed; a
+// tuning candidate for every K.  Tiles stay in the storage type (BF16 rows
+// are widened as they enter registers).  The rotated filter of a chunk's
+// channel goes to one of two buffers (chunk parity), written by the g warps.
+template <int K, typename T>
+struct RingShape {
+  using G = Geo<K, sizeof(T)>;
+  static constexpr int NT = kThreads;
+  static constexpr int GT = dw_groups<K>();
+  static constexpr int WPG = 4 / GT;
+  static constexpr int AT = (K + GT - 1) / GT;
+  static constexpr int DW_ROWS = kBwdTileH / WPG;
+  static constexpr int BR = bwd_block_rows<K>();
+  static constexpr int ROWS = kBwdTileH + 2 * G::R;
+  static constexpr int T_BYTES = round_up(ROWS * G::SP * (int)sizeof(T), 128);
+  static constexpr int STAGE_BYTES = 2 * T_BYTES;  // x, then dy (both with the halo)
+  static constexpr int NS = 2;
+  static constexpr int SM_W = NS * STAGE_BYTES;
+  static constexpr int SM_RED = SM_W + 2 * Geo<K>::WPAD * 4;
+  static constexpr int SM_BAR = round_up(SM_RED + 4 * AT * K * 4, 8);
+  static constexpr int SM_BYTES = SM_BAR + NS * 8 + 8;
+  static_assert(DW_ROWS % BR == 0 && 16 % BR == 0, "whole row blocks");
+  static_assert(SM_BYTES <= 227 * 1024, "shared memory");
+};
+
+template <typename T, int K>
+__global__ void __launch_bounds__(kThreads, 1)
+    dw_bwd_ring_kernel(const __grid_constant__ CUtensorMap tmx,
+                       const __grid_constant__ CUtensorMap tmdy, const T* __restrict__ x,
+                       const T* __restrict__ dy, const float* __restrict__ w, T* __restrict__ dx,
+                       float* __restrict__ partials, int C, int H, int W, FastDiv ftx,
+                       int tiles_per_plane, FastDiv fcpp, int tpc, int num_chunks, int clamp,
+                       int vec, int use_tma, int* err) {
+  using G = Geo<K, sizeof(T)>;
+  using S = RingShape<K, T>;
+  constexpr int KP = Geo<K>::KP;
+  extern __shared__ __align__(128) float smem[];
+  char* sm = reinterpret_cast<char*>(smem);
+  float* sm_red = reinterpret_cast<float*>(sm + S::SM_RED);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + S::SM_BAR);
+  volatile int* s_abort = reinterpret_cast<volatile int*>(sm + S::SM_BAR + S::NS * 8);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const bool dw_warp = warp >= 4;
+  const int wl = warp & 3;
+  const int g = wl % S::GT, part = wl / S::GT;
+  const int a_lo = group_lo(g, K, S::GT);
+  const int nrows = group_lo(g + 1, K, S::GT) - a_lo;
+
+  struct Item {
+    int q;
+    int t, t_end;
+  };
+  auto tile_origin = [&](int t, int& ty0, int& tx0) {
+    const uint32_t r = fdiv((uint32_t)t, ftx);
+    ty0 = (int)r * kBwdTileH;
+    tx0 = (t - (int)(r * ftx.d)) * kTileW;
+  };
+  auto first_tile = [&](Item& it) {
+    const int ch = it.q - (int)(fdiv((uint32_t)it.q, fcpp) * fcpp.d);
+    it.t = ch * tpc;
+    it.t_end = min(it.t + tpc, tiles_per_plane);
+  };
+  auto advance = [&](Item& it) {
+    if (++it.t == it.t_end) {
+      it.q += gridDim.x;
+      if (it.q < num_chunks) first_tile(it);
+    }
+  };
+  auto stage = [&](const Item& it, int sb) {
+    const int plane = (int)fdiv((uint32_t)it.q, fcpp);
+    int ty0, tx0;
+    tile_origin(it.t, ty0, tx0);
+    T* sx = reinterpret_cast<T*>(sm + sb * S::STAGE_BYTES);
+    T* sdy = reinterpret_cast<T*>(sm + sb * S::STAGE_BYTES + S::T_BYTES);
+    if (use_tma) {
+      if (threadIdx.x == 0) {
+        fence_proxy_async();
+        mbar_expect_tx(bars + sb, (uint32_t)(2 * S::ROWS * G::SP * (int)sizeof(T)));
+        tma_load_3d(sx, &tmx, tx0 - G::RP, ty0 - G::R, plane, bars + sb);
+        tma_load_3d(sdy, &tmdy, tx0 - G::RP, ty0 - G::R, plane, bars + sb);
+      }
+    } else {
+      const int64_t off = (int64_t)plane * H * W;
+      stage_tile<T, G::R, G::RP, G::SP, S::NT, false>(sx, x + off, H, W, ty0, tx0, S::ROWS,
+                                                      clamp != 0, vec != 0);
+      stage_tile<T, G::R, G::RP, G::SP, S::NT, false>(sdy, dy + off, H, W, ty0, tx0, S::ROWS,
+                                                      false, vec != 0);
+    }
+  };
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < S::NS; ++i) mbar_init(bars + i, 1);
+    *s_abort = 0;
+    mbar_init_fence();
+  }
+  cta_barrier();
+
+  Item pf{(int)blockIdx.x, 0, 0};
+  if (pf.q >= num_chunks) return;
+  first_tile(pf);
+  Item cs = pf;
+  uint32_t phase = 0;    // bit s: parity of the next TMA completion on stage s
+  uint32_t pending = 0;  // bit s: a TMA load into stage s is in flight
+#pragma unroll
+  for (int i = 0; i < S::NS - 1; ++i) {
+    if (pf.q < num_chunks) {
+      if (use_tma) pending |= 1u << i;
+      stage(pf, i);
+      advance(pf);
+    }
+    cp_async_commit();
+  }
+
+  float acc[S::AT][K];
+#pragma unroll
+  for (int s = 0; s < S::AT; ++s)
+#pragma unroll
+    for (int b = 0; b < K; ++b) acc[s][b] = 0.f;
+  int nchunk = 0;  // chunks this CTA has finished (filter buffer parity)
+  bool chunk_start = true;
+
+  for (int sb = 0; cs.q < num_chunks; sb = (sb + 1 == S::NS) ? 0 : sb + 1) {
+    // refill the stage released at the end of the previous item
+    if (pf.q < num_chunks) {
+      const int ps = sb == 0 ? S::NS - 1 : sb - 1;
+      if (use_tma) pending |= 1u << ps;
+      stage(pf, ps);
+      advance(pf);
+    }
+    cp_async_commit();
+    const int plane = (int)fdiv((uint32_t)cs.q, fcpp);
+    float* swf = reinterpret_cast<float*>(sm + S::SM_W) + (nchunk & 1) * Geo<K>::WPAD;
+    if (!dw_warp && chunk_start) {
+      // the rotated filter of this chunk's channel; the other buffer may still
+      // be read by the previous chunk's last tile
+      const float* wc = w + (int64_t)(plane % C) * K * K;
+      for (int k = threadIdx.x; k < K * KP; k += 128) {
+        const int a = k / KP, b = k - (k / KP) * KP;
+        swf[k] = b < K ? wc[(K - 1 - a) * K + (K - 1 - b)] : 0.f;
+      }
+    }
+    cp_async_wait_group<S::NS - 1>();  // the current item's cp.async copies have landed
+    if (pending & (1u << sb)) {
+      if (!mbar_wait(bars + sb, (phase >> sb) & 1u)) {
+        record_error(err, kDevErrTimeout);
+        *s_abort = 1;
+      }
+      phase ^= 1u << sb;
+      pending &= ~(1u << sb);
+    }
+    cta_barrier();
+    if (*s_abort) break;
+    T* sx = reinterpret_cast<T*>(sm + sb * S::STAGE_BYTES);
+    const T* sdy = reinterpret_cast<const T*>(sm + sb * S::STAGE_BYTES + S::T_BYTES);
+    int ty0, tx0;
+    tile_origin(cs.t, ty0, tx0);
+    if (use_tma && clamp &&
+        (ty0 - G::R < 0 || ty0 + kBwdTileH + G::R > H || tx0 - G::RP < 0 ||
+         tx0 + kTileW + G::RP > W))
+      clamp_fix<T, G::SP, S::NT>(sx, H, W, ty0, tx0, G::R, G::RP, S::ROWS);
+    if (!dw_warp) {
+#pragma unroll 1
+      for (int pass = 0; pass < 16 / S::BR; ++pass) {
+        const int r0 = wl * 16 + pass * S::BR;
+        float o[S::BR][4];
+        fwd_block<K, S::BR, T>(sdy + r0 * G::SP + 4 * lane, swf, o);
+        store_block<T, S::BR>(dx + (int64_t)plane * H * W, H, W, ty0 + r0, tx0 + 4 * lane,
+                              vec != 0, o);
+      }
+    } else {
+      const int r0 = part * S::DW_ROWS;
+      dw_rows<K, S::AT, S::GT, G::SP, S::BR, T>(sdy + (r0 + G::R) * G::SP + G::RP + 4 * lane,
+                                                sx + (r0 + a_lo) * G::SP + 4 * lane,
+                                                S::DW_ROWS / S::BR, nrows, acc);
+    }
+    const bool chunk_end = cs.t + 1 == cs.t_end;
+    if (chunk_end && dw_warp) {
+#pragma unroll
+      for (int s = 0; s < S::AT; ++s)
+#pragma unroll
+        for (int b = 0; b < K; ++b) {
+          float v = acc[s][b];
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+          if (lane == 0) sm_red[(wl * S::AT + s) * K + b] = v;
+          acc[s][b] = 0.f;
+        }
+    }
+    cta_barrier();  // stage sb is free again; sm_red is complete
+    if (chunk_end) {
+      for (int k = threadIdx.x; k < K * K; k += S::NT) {
+        const int a = k / K, b = k - (k / K) * K;
+        int gg = 0;
+        while (gg + 1 < S::GT && group_lo(gg + 1, K, S::GT) <= a) ++gg;
+        const int s = a - group_lo(gg, K, S::GT);
+        float sum = 0.f;
+        for (int p = 0; p < S::WPG; ++p) sum += sm_red[((p * S::GT + gg) * S::AT + s) * K + b];
+        partials[(int64_t)cs.q * K * K + k] = sum;
+      }
+      ++nchunk;
+      // sm_red is rewritten no earlier than the next chunk end, after another barrier
+    }
+    chunk_start = chunk_end;
+    advance(cs);
+  }
+  cp_async_wait_group<0>();
+  // after an abort: let the TMA loads still in flight land (bounded) before exiting
+  for (int s = 0; s < S::NS; ++s)
+    if (pending & (1u << s)) mbar_wait(bars + s, (phase >> s) & 1u);
+}
+
 }  // namespace giga

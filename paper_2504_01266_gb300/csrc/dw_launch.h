@@ -29,6 +29,12 @@ cudaError_t dw_sep_launch(const DwArgs& a, const float* wcol, const float* wrow,
 template <int K>
 cudaError_t dw_bwd_launch(const DwArgs& a, const DwConfig& cfg, cudaStream_t st);
 
+// Both gradients by the persistent kernel with a two-stage (x, dy) ring:
+// g (the input gradient before the clamp edge fold) and the filter partials
+// in the layout of dw_filter_launch (chunks of cfg.tiles_per_cta tiles).
+template <int K>
+cudaError_t dw_bwd_ring_launch(const DwArgs& a, const DwConfig& cfg, cudaStream_t st);
+
 // Filter gradient alone (persistent multi-stage kernel).  Writes
 // partials[planes * chunks][K*K] in the same layout as dw_bwd_launch.
 template <int K>
@@ -83,6 +89,8 @@ cudaError_t dw_finalize_launch(const DwArgs& a, int64_t chunks_per_plane, cudaSt
 #define GIGA_DW_EXTERN_BWD(K)                                                              \
   extern template cudaError_t dw_bwd_launch<K>(const DwArgs&, const DwConfig&,            \
                                                cudaStream_t);                              \
+  extern template cudaError_t dw_bwd_ring_launch<K>(const DwArgs&, const DwConfig&,       \
+                                                    cudaStream_t);                         \
   extern template cudaError_t dw_filter_launch<K>(const DwArgs&, const DwConfig&,         \
                                                   cudaStream_t);
 GIGA_DW_EXTERN(1) GIGA_DW_EXTERN(3) GIGA_DW_EXTERN(5) GIGA_DW_EXTERN(7)

@@ -131,6 +131,57 @@ cudaError_t dw_bwd_launch(const DwArgs& a, const DwConfig& cfg, cudaStream_t st)
 }
 
 template <typename T, int K>
+static cudaError_t bwd_ring_impl(const DwArgs& a, const DwConfig& cfg, cudaStream_t st) {
+  using S = RingShape<K, T>;
+  const size_t smem = (size_t)S::SM_BYTES;
+  auto kern = dw_bwd_ring_kernel<T, K>;
+  cudaError_t e = set_smem_once<dw_bwd_ring_kernel<T, K>>(smem);
+  if (e != cudaSuccess) return e;
+  static int ctas_per_sm[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int& per_sm = ctas_per_sm[dev & 63];
+  if (per_sm == 0) {
+    int v = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kern, S::NT, smem) != cudaSuccess ||
+        v < 1)
+      v = 1;
+    per_sm = v;
+  }
+  const int64_t tiles_x = (a.W + kTileW - 1) / kTileW;
+  const int64_t tiles_y = (a.H + kBwdTileH - 1) / kBwdTileH;
+  const int64_t chunks = dw_bwd_chunks_per_plane(a.H, a.W, cfg.tiles_per_cta);
+  const int64_t num_chunks = a.N * a.C * chunks;
+  const int64_t grid = std::min<int64_t>(num_chunks, (int64_t)per_sm * sm_count());
+  if (num_chunks + grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  CUtensorMap tmx, tmdy;
+  std::memset(&tmx, 0, sizeof(tmx));
+  std::memset(&tmdy, 0, sizeof(tmdy));
+  int use_tma = 0;
+  constexpr int es = sizeof(T);
+  if (plane_tma_ok(a.x, es, a.W) && plane_tma_ok(a.dy, es, a.W))
+    use_tma = make_plane_map(&tmx, a.x, es, a.W, a.H, a.N * a.C, Geo<K, es>::SP, S::ROWS) &&
+              make_plane_map(&tmdy, a.dy, es, a.W, a.H, a.N * a.C, Geo<K, es>::SP, S::ROWS);
+  kern<<<(unsigned)grid, S::NT, smem, st>>>(
+      tmx, tmdy, static_cast<const T*>(a.x), static_cast<const T*>(a.dy), a.w,
+      static_cast<T*>(a.dx), a.partials, (int)a.C, (int)a.H, (int)a.W,
+      make_fastdiv((uint32_t)tiles_x), (int)(tiles_x * tiles_y), make_fastdiv((uint32_t)chunks),
+      cfg.tiles_per_cta, (int)num_chunks, a.border, a.vec, use_tma, dw_error_word());
+  note_launch();
+  return cudaGetLastError();
+}
+
+template <int K>
+cudaError_t dw_bwd_ring_launch(const DwArgs& a, const DwConfig& cfg, cudaStream_t st) {
+  if constexpr (K > kMaxKFilter) {
+    return cudaErrorInvalidValue;
+  } else {
+    return a.dtype == 0 ? bwd_ring_impl<float, K>(a, cfg, st)
+                        : bwd_ring_impl<__nv_bfloat16, K>(a, cfg, st);
+  }
+}
+
+template <typename T, int K>
 static cudaError_t filter_impl(const DwArgs& a, const DwConfig& cfg, cudaStream_t st) {
   using S = FilterShape<K, T>;
   const size_t smem = (size_t)S::SM_BYTES;
@@ -239,6 +290,7 @@ cudaError_t dw_sep_launch(const DwArgs& a, const float* wcol, const float* wrow,
   template cudaError_t dw_sep_launch<K>(const DwArgs&, const float*, const float*, cudaStream_t);
 #define GIGA_DW_INSTANTIATE_BWD(K)                                                        \
   template cudaError_t dw_bwd_launch<K>(const DwArgs&, const DwConfig&, cudaStream_t);      \
+  template cudaError_t dw_bwd_ring_launch<K>(const DwArgs&, const DwConfig&, cudaStream_t); \
   template cudaError_t dw_filter_launch<K>(const DwArgs&, const DwConfig&, cudaStream_t);
 
 }  // namespace giga

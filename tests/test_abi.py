@@ -132,6 +132,8 @@ def test_autotune_set_choice(lib):
     try:
         d = dw(N=2, C=3, H=256, W=512, K=15)
         fused = _lib.GIGA_OP_BWD_INPUT | _lib.GIGA_OP_BWD_FILTER
+        assert _lib.giga_autotune_set_choice(d, fused, 6) == _lib.GIGA_OK
+        assert _lib.giga_autotune_set_choice(d, fused, 7) == _lib.GIGA_ERR_INVALID_ARG
         assert _lib.giga_autotune_set_choice(d, fused, 5) == _lib.GIGA_OK
         assert _lib.giga_autotune_choice(d, fused) == 5
         assert _lib.giga_autotune_choice(d, _lib.GIGA_OP_FWD) == 0  # other ops untouched

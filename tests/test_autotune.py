@@ -16,8 +16,8 @@ from helpers import assert_fp32, poison_like, to_np
 pytestmark = pytest.mark.gpu
 
 SHAPE = (2, 3, 520, 1000)
-# candidates per op: forward / input gradient 8, filter gradient 5, fused 6
-OPS = {1: 8, 2: 8, 4: 5, 6: 6}
+# candidates per op: forward / input gradient 8, filter gradient 5, fused 7
+OPS = {1: 8, 2: 8, 4: 5, 6: 7}
 
 
 @pytest.fixture(scope="module")

@@ -221,8 +221,8 @@ def test_fwd_every_configuration(giga, tmp_path, K, border, dtype, W):
 def test_bwd_every_configuration(giga, tmp_path, K, border, dtype, W):
     """Every filter-gradient configuration (tiles per chunk of the persistent
     filter kernel) and every fused-backward configuration (the fused kernel
-    with each tiles-per-CTA choice, and the two-pass split) against the FP64
-    oracle.  16 planes of 520 x W hold 1152 tiles of 64 x 128: with 1 or 2
+    with each tiles-per-CTA choice, the two-pass split, and the persistent
+    kernel with a two-stage tile ring) against the FP64 oracle.  16 planes of 520 x W hold 1152 tiles of 64 x 128: with 1 or 2
     tiles per chunk every persistent CTA runs several chunks back to back,
     so the shared-memory ring carries copies across chunk boundaries."""
     shape = (4, 4, 520, 998)
@@ -255,7 +255,7 @@ def test_bwd_every_configuration(giga, tmp_path, K, border, dtype, W):
             _force_candidates(tmp_path, shape, K, border, dtype, {2: cand})
             check_dw(giga.conv2d_bwd_filter(xc, dyc, K, border, out=nan_dw()),
                      (K, border, dtype, "filter", cand))
-        for cand in range(6):
+        for cand in range(7):
             _force_candidates(tmp_path, shape, K, border, dtype, {3: cand})
             dx, dw = giga.conv2d_bwd(xc, dyc, wc, border, dx=poison_like(dyc), dw=nan_dw())
             check_dx(dx, (K, border, dtype, "fused", cand))
