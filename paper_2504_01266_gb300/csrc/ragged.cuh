@@ -6,9 +6,16 @@
 //  * the host cuts every (image, channel) into chunks of up to 4 tiles of
 //    64 x 128 pixels (1 to 32, powers of 2: the plan's autotuner times them) and
 //    sorts the chunks longest first (cost K^2 per pixel);
-//  * CTAs (one per SM, 12 warps) pull chunk numbers from an atomic counter,
+//  * CTAs (one per SM, 16 warps) pull chunk numbers from an atomic counter,
 //    stage each tile's x and dy once, and run the three ops on it with fixed
-//    warp roles: warps 0-3 forward, 4-7 input gradient, 8-11 filter gradient;
+//    warp roles: warps 0-3 forward, 4-7 input gradient, 8-15 filter gradient.
+//    The filter gradient's per-pixel work equals each other role's, but its
+//    inner loop reaches a lower FMA rate; for K >= 11 all 8 of its warps work
+//    (in groups of at most 3 filter rows, so the union of the filter-size
+//    bodies fits the 128 registers a thread of a 16-warp CTA has) and the
+//    three roles finish a tile at about the same time; for K <= 9, where the
+//    forward and input-gradient roles bound the tile, 4 of them work (the
+//    other 4 stage and synchronise only: 8 working warps measured no faster);
 //  * each chunk writes one K*K vector of FP32 filter-gradient partials; the
 //    CTA that completes the last chunk of an (image, channel) -- detected with
 //    a per-(image, channel) atomic counter after a memory fence -- sums that
@@ -21,7 +28,8 @@
 
 namespace giga {
 
-constexpr int kRagThreads = 384;
+constexpr int kRagThreads = 512;
+constexpr int kRagDwWarps = 8;  // filter-gradient warps (warps 8-15)
 constexpr int kRagTilesPerChunk = 4;  // the plan's default; the autotuner may pick 1 to 32
 constexpr int kRagMaxK = 15;
 
@@ -55,11 +63,25 @@ struct RagParams {
   int border;
 };
 
+// Filter-row groups of the 8 filter-gradient warps for K >= 11: fewer rows
+// per warp keep the accumulators within the 128 registers a thread of a
+// 16-warp CTA has (K = 11: 4 groups of at most 3 rows; K >= 13: 8 groups of
+// at most 2 rows, one warp each).
+template <int K>
+constexpr int rag_groups() {
+  return K <= 7 ? 1 : (K <= 9 ? 2 : (K <= 11 ? 4 : 8));
+}
+// filter-gradient warps that work for this K (the others only stage and sync)
+template <int K>
+constexpr int rag_dw_active() {
+  return K <= 9 ? 4 : 8;
+}
+
 template <int K, typename T>
 struct RagShape {
   using G = Geo<K, sizeof(T)>;
-  static constexpr int GT = dw_groups<K>();
-  static constexpr int WPG = 4 / GT;
+  static constexpr int GT = K <= 9 ? dw_groups<K>() : rag_groups<K>();
+  static constexpr int WPG = rag_dw_active<K>() / GT;
   static constexpr int AT = (K + GT - 1) / GT;
   static constexpr int DW_ROWS = kBwdTileH / WPG;
   static constexpr int ROWS = kBwdTileH + 2 * G::R;
@@ -76,9 +98,9 @@ struct RagLayout {
   static constexpr int STAGE = 2 * TILE;          // x, then dy
   static constexpr int WB = G::WPAD * 4;          // one filter
   static constexpr int FILT = 2 * STAGE;          // [2][w, wf]
-  static constexpr int RED = FILT + 4 * WB;       // 4 dw warps x max(AT * K) floats
+  static constexpr int RED = FILT + 4 * WB;       // [2 chunks][w, wf] filters
   static constexpr int RED_FLOATS = 66;           // K = 11: 6 rows x 11 taps
-  static constexpr int INTS = RED + 4 * RED_FLOATS * 4;
+  static constexpr int INTS = RED + kRagDwWarps * RED_FLOATS * 4;
   static constexpr int SM_BYTES = INTS + 16;
   static_assert(RagShape<11, T>::AT * 11 <= RED_FLOATS && RagShape<15, T>::AT * 15 <= RED_FLOATS,
                 "reduction rows");
@@ -146,7 +168,7 @@ __device__ __forceinline__ int rag_chunk(const RagParams& p, const RagChunk& ch,
   T* dxp = do_dx ? static_cast<T*>(im.dx) + off : nullptr;
   const float* wc = (do_fwd || do_dx) ? im.w + (int64_t)ch.channel * KK : nullptr;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int role = warp >> 2, wl = warp & 3;
+  const int role = warp < 8 ? warp >> 2 : 2, wl = warp < 8 ? (warp & 3) : warp - 8;
   const int g = wl % S::GT;
   const int part = wl / S::GT;
   const int a_lo = group_lo(g, K, S::GT);
@@ -185,7 +207,7 @@ __device__ __forceinline__ int rag_chunk(const RagParams& p, const RagChunk& ch,
           store_block<T, BR>(dst, H, W, ty0 + r0, tx0 + 4 * lane, vec, o);
         }
       }
-    } else if (do_dw) {
+    } else if (do_dw && wl < rag_dw_active<K>()) {
       constexpr int BR = bwd_block_rows<K>();
       const int r0 = part * S::DW_ROWS;
       dw_rows<K, S::AT, S::GT, G::SP, BR, T>(sdy + (r0 + G::R) * G::SP + G::RP + 4 * lane,
@@ -198,7 +220,7 @@ __device__ __forceinline__ int rag_chunk(const RagParams& p, const RagChunk& ch,
 
   // filter-gradient partial of this chunk: warp butterflies, then a fixed-order
   // sum over the group's warps
-  if (role == 2 && do_dw) {
+  if (role == 2 && do_dw && wl < rag_dw_active<K>()) {
 #pragma unroll
     for (int s = 0; s < S::AT; ++s)
 #pragma unroll
