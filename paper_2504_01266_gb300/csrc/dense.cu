@@ -5,20 +5,24 @@
 //
 // is, for each tile of 128 consecutive output pixels of one image row, a
 // 128 x 64 x 576 GEMM: M = pixels, N = output channels, K = (tap, input
-// channel).  The 576-long K is walked as 9 taps x 64 channels; for tap (a, b)
-// the A operand is the 128 x 64 block of x shifted by (a - 1, b - 1), which a
-// TMA tensor load fetches directly from the NHWC tensor (out-of-range pixels
-// arrive as zeros: the zero border).  The GigaAPI paper only remarks that
+// channel).  The kernels here organise it around input-row bands: one TMA
+// load brings 130 pixels of one input row (the tile plus its one-pixel halo;
+// out-of-range pixels arrive as zeros, the zero border), and that band viewed
+// from pixel b, times the weights of the three taps (0, b), (1, b), (2, b),
+// is ONE MMA of N = 192 whose three 64-column blocks are the accumulators of
+// the three output rows the band feeds.  The GigaAPI paper only remarks that
 // convolution benefits from matrix multiplication (Section 3.1); this is that
 // contraction done on tcgen05.
 //
-// One persistent CTA per SM, 6 warps:
+// Forward / input gradient: one persistent CTA per SM, 6 warps:
 //   warp 0    TMA producer: all 9 weight taps once (72 KB, resident), then the
-//             shifted activation blocks through a 6-stage ring (16 KB each);
-//   warp 1    allocates 128 TMEM columns (two 64-column FP32 accumulators) and
-//             one lane issues the tcgen05.mma chain (4 x K=16 per tap);
-//   warps 2-5 epilogue: tcgen05.ld of the accumulator (each warp reads its
-//             32-lane TMEM quadrant), convert to BF16, store the pixel rows.
+//             bands through a 6-slot ring;
+//   warp 1    allocates 512 TMEM columns (a ring of 8 accumulators of 64
+//             columns, one per output row) and one lane issues the MMAs
+//             (3 pixel shifts x 4 K-steps of 16 per band);
+//   warps 2-5 epilogue: tcgen05.ld of a finished row's accumulator (each warp
+//             its 32-lane TMEM quadrant), re-zero it, convert to BF16, stage
+//             the row swizzled in shared memory, one TMA store per tile.
 // Operands are K-major with the 128-byte swizzle the TMA writes.  Every
 // mbarrier wait is bounded: on expiry the CTA records an error code, stops
 // issuing work and frees its TMEM (the host reads the code back).
@@ -158,9 +162,10 @@ __device__ __forceinline__ void dense_fail(int* err, volatile int* abort_flag) {
 }
 
 // Work order: output-row tiles (n, strip jt, row i), i fastest; CTA b owns the
-// contiguous range [b*T/G, (b+1)*T/G).  A run of consecutive rows of one strip
-// needs input rows i0 - 1 .. i1 (130-pixel bands with the one-pixel halo on
-// each side), each loaded ONCE into a ring slot; output row i reads the bands
+// contiguous range [b*T/G, (b+1)*T/G).  A run of consecutive rows i0 .. i1 - 1
+// of one strip (at most kAccBufs rows, see run_end_of) needs input rows
+// i0 - 1 .. i1 (130-pixel bands with the one-pixel halo on each side), each
+// loaded once per run into a ring slot; output row i reads the bands
 // of rows i - 1, i, i + 1, and tap (a, b) is the band of row i + a - 1 viewed
 // from pixel b (a start address b * 128 bytes into the slot).
 constexpr int kBandPx = kDenseTileM + 2;              // 130 pixels
@@ -175,6 +180,18 @@ constexpr size_t kDenseSmemBand = 1024 + kDenseTaps * kDenseBBytes + kBandSlots 
 __device__ __forceinline__ void tile_range(int64_t total, int64_t& begin, int64_t& end) {
   begin = total * blockIdx.x / gridDim.x;
   end = total * (blockIdx.x + 1) / gridDim.x;
+}
+
+// End of the run of output rows that starts at `tile`: a run stays inside one
+// strip and inside one aligned group of kAccBufs rows in CTA order, so the
+// rows any band touches own consecutive TMEM blocks and every MMA writes one
+// contiguous column range.  (An MMA pair that straddled the end of the block
+// ring ran at about 60 % of the rate of one contiguous MMA; the cost of the cap
+// is two halo bands re-loaded, mostly from L2, per group of rows.)
+__device__ __forceinline__ int64_t run_end_of(int64_t tile, int64_t t_begin, int64_t t_end, int H) {
+  const int64_t strip_end = (tile / H + 1) * (int64_t)H;
+  const int64_t group_end = t_begin + ((tile - t_begin) / kAccBufs + 1) * kAccBufs;
+  return min(t_end, min(strip_end, group_end));
 }
 
 __global__ void __launch_bounds__(kDenseThreads, 1)
@@ -240,7 +257,7 @@ __global__ void __launch_bounds__(kDenseThreads, 1)
         // a run of rows of one strip: [tile, run_end)
         const int i0 = (int)(tile % p.H);
         const int64_t strip = tile / p.H;  // n * tiles_w + jt
-        const int64_t run_end = min(t_end, (strip + 1) * (int64_t)p.H);
+        const int64_t run_end = run_end_of(tile, t_begin, t_end, p.H);
         const int i1 = i0 + (int)(run_end - tile);
         const int jt = (int)(strip % p.tiles_w);
         const int n = (int)(strip / p.tiles_w);
@@ -263,8 +280,9 @@ __global__ void __launch_bounds__(kDenseThreads, 1)
       // rho, rho - 1 through taps a = 0, 1, 2: one MMA of N = 64 * (number of
       // those rows inside the run) into their accumulators.  Output row number
       // o (in CTA order) owns TMEM block acc_block(o) = R - 1 - (o mod R), so
-      // rows o + 1, o, o - 1 sit in ascending blocks (split where the ring
-      // wraps).  Blocks arrive zeroed from the epilogue; every MMA accumulates.
+      // rows o + 1, o, o - 1 sit in ascending blocks, contiguous because a run
+      // never crosses a multiple of R in o.  Blocks arrive zeroed from the
+      // epilogue; every MMA accumulates.
       bool ok = mbar_wait(bfull, 0);
       if (!ok) dense_fail(p.err, &s_abort);
       uint32_t seq = 0;   // band counter
@@ -273,8 +291,7 @@ __global__ void __launch_bounds__(kDenseThreads, 1)
       const uint32_t a_base = s_addr(sA);
       auto blk = [](int64_t o) { return kAccBufs - 1 - (int)(((o % kAccBufs) + kAccBufs) % kAccBufs); };
       for (int64_t tile = t_begin; ok && tile < t_end && !s_abort;) {
-        const int64_t strip = tile / p.H;
-        const int64_t run_end = min(t_end, (strip + 1) * (int64_t)p.H);
+        const int64_t run_end = run_end_of(tile, t_begin, t_end, p.H);
         const int rows = (int)(run_end - tile);
         for (int k = 0; k < rows + 2 && ok; ++k) {
           // band k of the run is input row i0 - 1 + k; output row (run-local) k - 1
@@ -297,24 +314,20 @@ __global__ void __launch_bounds__(kDenseThreads, 1)
             }
           }
           tc_fence_after();
+          // the na rows sit in blocks q0 .. q0 + na - 1 <= kAccBufs - 1: a run
+          // never leaves its aligned group of kAccBufs rows
           const int na = a_hi - a_lo + 1;
           const int q0 = blk(o_rho + 1 - a_lo);
-          const int n1 = min(na, kAccBufs - q0);  // taps before the ring wraps
+          const uint32_t idesc = kDenseIdescN(64 * na);
+          const uint32_t d_addr = tmem_base + (uint32_t)(q0 * 64);
           const uint32_t a_slot = a_base + (band % kBandSlots) * kSlotBytes;
 #pragma unroll 1
           for (int b = 0; b < 3; ++b) {
             const uint32_t a_row = a_slot + b * 128;
             const uint32_t b_row = b_base + (b * 3 + a_lo) * kDenseBBytes;
 #pragma unroll
-            for (int kk = 0; kk < kDenseC / 16; ++kk) {
-              tc_mma(tmem_base + (uint32_t)(q0 * 64), sw128_desc(a_row + 32 * kk),
-                     sw128_desc(b_row + 32 * kk),
-                     kDenseIdescN(64 * n1), 1u);
-              if (n1 < na)
-                tc_mma(tmem_base, sw128_desc(a_row + 32 * kk),
-                       sw128_desc(b_row + n1 * kDenseBBytes + 32 * kk),
-                       kDenseIdescN(64 * (na - n1)), 1u);
-            }
+            for (int kk = 0; kk < kDenseC / 16; ++kk)
+              tc_mma(d_addr, sw128_desc(a_row + 32 * kk), sw128_desc(b_row + 32 * kk), idesc, 1u);
           }
           tc_commit(empty + band % kBandSlots);
           if (a_hi == 2) tc_commit(tfull + blk(o_rho - 1));  // row o_rho - 1 is complete
