@@ -89,14 +89,8 @@ __device__ __forceinline__ uint64_t sw128_desc_mn(uint32_t saddr, uint32_t lbo) 
   return d;
 }
 
-// Instruction descriptor: D FP32, A and B BF16, both K-major, M = 128, N = 64.
-constexpr uint32_t kDenseIdesc = (1u << 4)     // D format F32
-                               | (1u << 7)     // A format BF16
-                               | (1u << 10)    // B format BF16
-                               | ((64u >> 3) << 17)    // N
-                               | ((128u >> 4) << 24);  // M
-
-// M = 128, N = n (a multiple of 64 here), both operands K-major.
+// Instruction descriptor: D FP32, A and B BF16, both K-major, M = 128,
+// N = n (a multiple of 64 here).
 __device__ __forceinline__ uint32_t kDenseIdescN(int n) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((128u >> 4) << 24);
 }
@@ -431,41 +425,48 @@ __global__ void __launch_bounds__(kDenseThreads, 1)
 // ------------------------------------------------------- filter gradient
 //   dw[o][a][b][c] = sum_{n,i,j} dy[n][i][j][o] * x[n][i + a - 1][j + b - 1][c]
 // Work unit: a chunk of 64 pixel positions k = 0..63 at j0 + k of one image
-// row i.  Per chunk the producer loads three x bands (image rows i - 1, i,
-// i + 1; pixels j0 - 1 .. j0 + 63, 65 pixels x 64 channels, one 128-byte row
-// per pixel, 128-byte swizzle) and one dy band (row i, pixels j0 - 2 ..
-// j0 + 63), 34.6 KB; six stages are in flight.  Both are read as MN-major
-// operands (K = pixel position), a view b pixels into a band being a start
-// address b * 128 bytes in (the swizzle phase follows the absolute shared
-// address).  With A[k][c] = x[j0 + k - 1][c] (x band of tap row a, view 0)
-// and B_s[k][o] = dy[j0 + k - s][o] (dy band, view 2 - s):
+// row i.  A chunk needs three x bands (image rows i - 1, i, i + 1; pixels
+// j0 - 1 .. j0 + 63, 65 pixels x 64 channels, one 128-byte row per pixel,
+// 128-byte swizzle) and one dy band (row i, pixels j0 - 2 .. j0 + 63).  Both
+// are read as MN-major operands (K = pixel position), a view b pixels into a
+// band being a start address b * 128 bytes in (the swizzle phase follows the
+// absolute shared address).  With A[k][c] = x[j0 + k - 1][c] (x band of tap
+// row a, view 0) and B_s[k][o] = dy[j0 + k - s][o] (dy band, view 2 - s):
 //   sum_k A[k][c] B_s[k][o] = sum_p x[p + s - 1][c] dy[p][o],  p = j0 + k - s,
 // the contribution of tap (a, s) over the pixels p = j0 - s .. j0 + 63 - s.
 // The chunks of a row (ceil((W + 2) / 64) of them) tile every pixel once for
 // each s (dy is zero outside the image), so one MMA with N = 192 -- B = the
 // three shifts s = 2, 1, 0 as 64-column N blocks 128 bytes apart -- gives all
 // three taps of a filter row, and M = 128 stacks two filter rows (x bands of
-// rows a and a + 1, one band stride apart):
+// rows a and a + 1, one band slot apart):
 //   MMA 0: rows a = 0, 1 -> 6 taps;   MMA 1: row a = 2 (the second M half,
 //   band 2 viewed one pixel further, is computed and discarded).
-// 8 MMAs of 128 x 192 x 16 per chunk read 80 KB of operands instead of the
-// 120 KB of 20 MMAs of 128 x 64 x 16 with one tap pair each.  D accumulates in
-// TMEM over all chunks of the CTA (2 x 192 columns); each CTA then writes its
-// FP32 partial sums [tap][c][o] and a second kernel adds the CTAs' partials
-// in FP64 in CTA order.
+// Chunks are ordered (image, column strip, row), row fastest, and CTA b owns
+// a contiguous range of them, so consecutive chunks of a CTA walk down one
+// column strip: each x band is loaded ONCE per run of rows into a ring of
+// kWgXSlots slots and serves three chunks (rows i + 1, i, i - 1); dy bands go
+// through their own ring.  MMA 0 needs the bands of rows i - 1 and i one slot
+// apart: the band that lands in slot 0 is also written to a mirror slot after
+// the last one, so the pair (last slot, slot 0) is adjacent too.  D
+// accumulates in TMEM over all chunks of the CTA (2 x 192 columns); each CTA
+// then writes its FP32 partial sums [tap][c][o] and a second kernel adds the
+// CTAs' partials in FP64 in CTA order.
 constexpr int kWgTileP = 64;                           // pixel positions per chunk (MMA K: 4 x 16)
 constexpr int kWgXPx = kWgTileP + 1;                   // x band: 65 pixels
 constexpr int kWgDyPx = kWgTileP + 2;                  // dy band: 66 pixels
 constexpr int kWgSlot = 9 * 1024;                      // 1024-aligned band slots
-constexpr int kWgDyOff = 3 * kWgSlot;
-constexpr int kWgStageBytes = 4 * kWgSlot;             // 36 KB
-constexpr uint32_t kWgStageTx = (3 * kWgXPx + kWgDyPx) * kDenseC * 2;
-constexpr int kWgStages = 6;
+constexpr int kWgXSlots = 12;                          // x ring (plus one mirror slot)
+constexpr int kWgDySlots = 8;                          // dy ring
+constexpr uint32_t kWgXTx = kWgXPx * kDenseC * 2;
+constexpr uint32_t kWgDyTx = kWgDyPx * kDenseC * 2;
+constexpr int kWgDyOff = (kWgXSlots + 1) * kWgSlot;
+constexpr int kWgBarOff = kWgDyOff + kWgDySlots * kWgSlot;
 constexpr int kWgN = 192;                              // three 64-channel shifts
 constexpr int kWgTmemCols = 512;
-constexpr size_t kWgSmem = 1024 + kWgStages * kWgStageBytes + 256;
+constexpr size_t kWgSmem = 1024 + kWgBarOff + 512;
 constexpr int64_t kWgPartialFloats = (int64_t)kDenseTaps * kDenseC * kDenseC;
 static_assert(kWgSmem <= 227 * 1024, "filter-gradient shared memory");
+static_assert((2 * kWgXSlots + 2 * kWgDySlots + 1) * 8 + 4 <= 512, "barrier area");
 
 // M = 128, N = 192, both operands MN-major.
 constexpr uint32_t kWgIdesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) |
@@ -485,19 +486,29 @@ __global__ void __launch_bounds__(kDenseThreads, 1)
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem =
       reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kWgStages * kWgStageBytes);
-  uint64_t* full = bars;
-  uint64_t* empty = bars + kWgStages;
-  uint64_t* done = bars + 2 * kWgStages;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kWgStages + 1);
+  uint8_t* sx = smem;                 // x slots 0 .. kWgXSlots (the last mirrors slot 0)
+  uint8_t* sdy = smem + kWgDyOff;     // dy slots
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kWgBarOff);
+  uint64_t* xfull = bars;
+  uint64_t* xempty = bars + kWgXSlots;
+  uint64_t* dyfull = bars + 2 * kWgXSlots;
+  uint64_t* dyempty = bars + 2 * kWgXSlots + kWgDySlots;
+  uint64_t* done = bars + 2 * kWgXSlots + 2 * kWgDySlots;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
   __shared__ volatile int s_abort;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int64_t t_begin, t_end;
+  tile_range(p.num_tiles, t_begin, t_end);
 
   if (threadIdx.x == 0) {
     s_abort = 0;
-    for (int st = 0; st < kWgStages; ++st) {
-      mbar_init(full + st, 1);
-      mbar_init(empty + st, 1);
+    for (int q = 0; q < kWgXSlots; ++q) {
+      mbar_init(xfull + q, 1);
+      mbar_init(xempty + q, 1);
+    }
+    for (int q = 0; q < kWgDySlots; ++q) {
+      mbar_init(dyfull + q, 1);
+      mbar_init(dyempty + q, 1);
     }
     mbar_init(done, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -516,59 +527,90 @@ __global__ void __launch_bounds__(kDenseThreads, 1)
 
   if (warp == 0) {
     if (lane == 0) {
-      int stage = 0;
-      uint32_t phase = 0;
-      for (int64_t tile = blockIdx.x; tile < p.num_tiles && !s_abort; tile += gridDim.x) {
-        const int jt = (int)(tile % p.tiles_w);
-        const int64_t r = tile / p.tiles_w;
-        const int i = (int)(r % p.H), n = (int)(r / p.H);
-        const int j0 = jt * kWgTileP;
-        if (!mbar_wait(empty + stage, phase ^ 1)) {
+      // ---------------------------------------------------------- producer
+      // per run of rows i0 .. i1 - 1 of one strip: x bands i0 - 1 and i0, then
+      // per chunk i the x band i + 1 and the dy band i (the MMA issuer's order)
+      uint32_t xc = 0, dc = 0;  // x / dy band counters: slot c % S, phase (c / S) & 1
+      for (int64_t tile = t_begin; tile < t_end && !s_abort;) {
+        const int64_t strip = tile / p.H;  // n * tiles_w + jt
+        const int64_t run_end = min(t_end, (strip + 1) * (int64_t)p.H);
+        const int i0 = (int)(tile - strip * p.H);
+        const int rows = (int)(run_end - tile);
+        const int j0 = (int)(strip % p.tiles_w) * kWgTileP;
+        const int n = (int)(strip / p.tiles_w);
+        bool ok = true;
+        for (int q = -1; q <= rows && ok && !s_abort; ++q) {
+          // x band of image row i0 + q (rows -1 and H arrive as zeros)
+          const int sl = (int)(xc % kWgXSlots);
+          if (!(ok = mbar_wait(xempty + sl, ((xc / kWgXSlots) & 1) ^ 1))) break;
+          mbar_expect_tx(xfull + sl, sl == 0 ? 2 * kWgXTx : kWgXTx);
+          tma_load_4d(sx + sl * kWgSlot, &tmap_x, 0, j0 - 1, i0 + q, n, xfull + sl);
+          if (sl == 0)
+            tma_load_4d(sx + kWgXSlots * kWgSlot, &tmap_x, 0, j0 - 1, i0 + q, n, xfull + sl);
+          ++xc;
+          if (q < 1) continue;
+          // dy band of image row i0 + q - 1 (its chunk needs x rows up to i0 + q)
+          const int dl = (int)(dc % kWgDySlots);
+          if (!(ok = mbar_wait(dyempty + dl, ((dc / kWgDySlots) & 1) ^ 1))) break;
+          mbar_expect_tx(dyfull + dl, kWgDyTx);
+          tma_load_4d(sdy + dl * kWgSlot, &tmap_dy, 0, j0 - 2, i0 + q - 1, n, dyfull + dl);
+          ++dc;
+        }
+        if (!ok) {
           dense_fail(p.err, &s_abort);
           break;
         }
-        uint8_t* base = smem + stage * kWgStageBytes;
-        mbar_expect_tx(full + stage, kWgStageTx);
-        for (int a = 0; a < 3; ++a)
-          tma_load_4d(base + a * kWgSlot, &tmap_x, 0, j0 - 1, i + a - 1, n, full + stage);
-        tma_load_4d(base + kWgDyOff, &tmap_dy, 0, j0 - 2, i, n, full + stage);
-        if (++stage == kWgStages) {
-          stage = 0;
-          phase ^= 1;
-        }
+        tile = run_end;
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      int stage = 0;
-      uint32_t phase = 0;
+      // ------------------------------------------------------- MMA issuer
+      uint32_t xc = 0, dc = 0;  // same counters as the producer
       bool first = true, ok = true;
-      for (int64_t tile = blockIdx.x; tile < p.num_tiles && !s_abort; tile += gridDim.x) {
-        if (!mbar_wait(full + stage, phase)) {
+      const uint32_t x_base = s_addr(sx), dy_base = s_addr(sdy);
+      auto wait_x = [&](uint32_t c) {
+        return mbar_wait(xfull + c % kWgXSlots, (c / kWgXSlots) & 1);
+      };
+      for (int64_t tile = t_begin; ok && tile < t_end && !s_abort;) {
+        const int64_t strip = tile / p.H;
+        const int64_t run_end = min(t_end, (strip + 1) * (int64_t)p.H);
+        const int rows = (int)(run_end - tile);
+        ok = wait_x(xc) && wait_x(xc + 1);  // bands i0 - 1, i0
+        for (int k = 0; ok && k < rows; ++k) {
+          const uint32_t cb = xc + k;  // band of row i - 1 (i = i0 + k)
+          const uint32_t cd = dc + k;
+          if (!(ok = wait_x(cb + 2) &&
+                     mbar_wait(dyfull + cd % kWgDySlots, (cd / kWgDySlots) & 1)))
+            break;
+          tc_fence_after();
+          // MMA 0: bands i - 1 and i, one slot apart (the mirror after the last slot)
+          const uint32_t a0 = x_base + (cb % kWgXSlots) * kWgSlot;
+          // MMA 1: band i + 1 (second M half: the same band one pixel on, discarded)
+          const uint32_t a1 = x_base + ((cb + 2) % kWgXSlots) * kWgSlot;
+          const uint32_t b0 = dy_base + (cd % kWgDySlots) * kWgSlot;  // N block s' -> shift 2 - s'
+#pragma unroll
+          for (int kk = 0; kk < kWgTileP / 16; ++kk)
+            tc_mma(tmem_base, sw128_desc_mn(a0 + kk * 2048, kWgSlot),
+                   sw128_desc_mn(b0 + kk * 2048, 128), kWgIdesc, (first && kk == 0) ? 0u : 1u);
+#pragma unroll
+          for (int kk = 0; kk < kWgTileP / 16; ++kk)
+            tc_mma(tmem_base + 256u, sw128_desc_mn(a1 + kk * 2048, 128),
+                   sw128_desc_mn(b0 + kk * 2048, 128), kWgIdesc, (first && kk == 0) ? 0u : 1u);
+          first = false;
+          tc_commit(dyempty + cd % kWgDySlots);
+          tc_commit(xempty + cb % kWgXSlots);  // band i - 1 has had its last use
+        }
+        if (!ok) {
           dense_fail(p.err, &s_abort);
-          ok = false;
           break;
         }
-        tc_fence_after();
-        const uint32_t base = s_addr(smem + stage * kWgStageBytes);
-        const uint32_t dy_base = base + kWgDyOff;  // N block s' = 0, 1, 2 -> shift s = 2, 1, 0
-#pragma unroll
-        for (int g = 0; g < 2; ++g) {
-          const uint32_t a0 = base + g * 2 * kWgSlot;
-          const uint32_t lbo = g == 0 ? kWgSlot : 128;
-#pragma unroll
-          for (int k = 0; k < kWgTileP / 16; ++k) {
-            tc_mma(tmem_base + (uint32_t)(g * 256), sw128_desc_mn(a0 + k * 2048, lbo),
-                   sw128_desc_mn(dy_base + k * 2048, 128), kWgIdesc,
-                   (first && k == 0) ? 0u : 1u);
-          }
-        }
-        first = false;
-        tc_commit(empty + stage);
-        if (++stage == kWgStages) {
-          stage = 0;
-          phase ^= 1;
-        }
+        // the run's last two bands (rows i1 - 1 and i1) are no longer needed
+        tc_commit(xempty + (xc + rows) % kWgXSlots);
+        tc_commit(xempty + (xc + rows + 1) % kWgXSlots);
+        xc += rows + 2;
+        dc += rows;
+        tile = run_end;
       }
       if (ok) tc_commit(done);  // fires once every MMA above has completed
       else mbar_arrive(done);
