@@ -4,10 +4,14 @@ FP64 oracle, through the C ABI.
 
 Small cases span several output tiles with ragged tails (upsampled sides not
 multiples of the 64 x 128 tile, widths not multiples of 4), scales 1 to 20,
-both borders and both storage types; the fused pass must also equal, bit for
-bit in FP32, the two-call path (upsample, then the depthwise forward).  The
-4K-image workload is checked on sampled outputs and on every kind of border
-pixel.
+both borders and both storage types.  For K != 3 the fused pass must also
+equal, bit for bit in FP32, the two-call path (upsample, then the depthwise
+forward); for K = 3 the polyphase kernel adds the taps that land on one input
+pixel before multiplying, so its FP32 bound counts K^2 + 4 rounded terms and
+it is compared with the two-call path within that bound.  Every store width
+of the polyphase kernel (16, 8, 4 bytes and scalar, FP32 and BF16, aligned and
+offset outputs) is exercised.  The 4K-image workload is checked on sampled
+outputs and on every kind of border pixel.
 """
 import numpy as np
 import pytest
@@ -28,6 +32,12 @@ def giga():
     from paper_2504_01266_gb300 import build
     build.build()
     return g
+
+
+def n_terms(K, scale):
+    """Rounded terms of one FP32 output: K^2 multiply-adds, or for the K = 3
+    polyphase kernel (scale >= 2) up to 9 tap additions plus 4 multiply-adds."""
+    return K * K + 4 if (K == 3 and scale > 1) else K * K
 
 
 def make(shape, K, seed, dtype=torch.float32):
@@ -62,11 +72,43 @@ def test_upsample_conv2d_fp32(giga, K, border, shape, scale):
     b = BORDER[border]
     ref = oracle.upsample_dw_fwd(x.numpy(), w.numpy(), b, scale)
     mag = oracle.upsample_dw_fwd(np.abs(x.numpy()), np.abs(w.numpy()), b, scale)
-    assert_fp32(to_np(y), ref, mag, K * K, (shape, scale, K, border))
-    # the fused pass equals the two-call path bit for bit
+    assert_fp32(to_np(y), ref, mag, n_terms(K, scale), (shape, scale, K, border))
     up = giga.upsample_nearest(xc, scale)
     two = giga.conv2d_fwd(up, wc, border)
-    assert torch.equal(y, two), (shape, scale, K, border)
+    if K == 3 and scale > 1:
+        # polyphase: both within their bounds of the exact value
+        assert_fp32(to_np(y), to_np(two), 2 * mag, n_terms(K, scale), (shape, scale, "two"))
+    else:
+        # the fused pass equals the two-call path bit for bit
+        assert torch.equal(y, two), (shape, scale, K, border)
+
+
+@pytest.mark.parametrize("scale", [2, 3, 4, 5, 6, 8, 16])
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
+@pytest.mark.parametrize("offset", [0, 1])
+@pytest.mark.parametrize("border", ["zero", "clamp"])
+def test_polyphase_store_widths(giga, scale, dtype, offset, border):
+    """The K = 3 polyphase kernel at every store width: s a multiple of 8, 4,
+    2 or odd, FP32 and BF16, the output at an aligned address or one element
+    past it (scalar stores), widths and heights that leave partial warps and
+    CTAs (W = 37: lanes past the image; H = 70: a second row block)."""
+    shape = (1, 2, 70, 37)
+    x, w = make(shape, 3, 900 + scale + offset, dtype)
+    out_shape = shape[:2] + (shape[2] * scale, shape[3] * scale)
+    n_out = int(np.prod(out_shape))
+    buf = torch.full((n_out + 8,), float("nan"), dtype=dtype).cuda()
+    y = buf[offset:offset + n_out].view(out_shape)
+    giga.upsample_conv2d(x.cuda(), w.cuda(), scale, border, out=y)
+    b = BORDER[border]
+    xd = x.double().numpy() if dtype == torch.bfloat16 else x.numpy()
+    ref = oracle.upsample_dw_fwd(xd, w.numpy(), b, scale)
+    if dtype == torch.float32:
+        mag = oracle.upsample_dw_fwd(np.abs(x.numpy()), np.abs(w.numpy()), b, scale)
+        assert_fp32(to_np(y), ref, mag, n_terms(3, scale), (scale, offset, border))
+    else:
+        assert normwise(to_np(y), ref) <= BF16_KERNEL_TOL
+    # the guard elements around the output stay untouched
+    assert torch.isnan(buf[:offset]).all() and torch.isnan(buf[offset + n_out:]).all()
 
 
 @pytest.mark.parametrize("K", [3, 9])
@@ -118,6 +160,6 @@ def test_4k_image_sampled(giga, scale):
     ref = oracle.upsample_dw_fwd_points(x.numpy(), lap.numpy(), oracle.ZERO, scale, idx.numpy())
     mag = oracle.upsample_dw_fwd_points(x.numpy(), np.abs(lap.numpy()), oracle.ZERO, scale,
                                         idx.numpy())
-    assert_fp32(got, ref, mag, 9, ("4k", scale))
+    assert_fp32(got, ref, mag, n_terms(3, scale), ("4k", scale))
     del y
     torch.cuda.empty_cache()
