@@ -17,8 +17,11 @@
 // ones fill the tail.  One kernel per size keeps each size's own register
 // allocation and its filter taps in uniform registers; a single kernel
 // switching on K per tile measured 125 registers instead of at most 72.  The
-// per-tile body is the single-image kernel's (upsample.cuh), so every output
-// equals that of giga_upsample_conv2d_fwd on the image alone, bit for bit.
+// 3 x 3 class is numbered in the polyphase kernel's items instead (plane,
+// group of 8 input rows, 32 input columns) and run by persistent warps.  The
+// per-tile and per-item bodies are the single-image kernels' (upsample.cuh),
+// so every output equals that of giga_upsample_conv2d_fwd on the image alone,
+// bit for bit.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -43,9 +46,12 @@ struct UpRagImage {
   const float* w;
   int tile_base;  // number of this image's first tile
   int H, W, C, K, Ho, Wo;
-  int tiles_x, tiles_y, n_tiles;  // n_tiles = C * tiles_x * tiles_y
+  int tiles_x, tiles_y, n_tiles;  // n_tiles = C * tiles_x * tiles_y (K = 3: polyphase items)
   int vec;
   FastDiv fs;
+  int mode;       // K = 3: the polyphase compilation (up3_mode)
+  FastDiv fcb;    // K = 3: 32-column blocks per row group
+  FastDiv fpp;    // K = 3: items per plane
 };
 
 // One launch: the images img_lo..img_hi of one filter size, whose tiles are
@@ -107,10 +113,41 @@ __global__ void __launch_bounds__(kThreads) up_rag_kernel(UpRagParams p) {
   up_rag_body<T, K>(p);
 }
 
-// FP32 K = 3 compiled for five CTAs per SM, as the single-image pass.
-template <typename T, int K>
-__global__ void __launch_bounds__(kThreads, 5) up_rag_kernel_hi_occ(UpRagParams p) {
-  up_rag_body<T, K>(p);
+// The 3 x 3 class: persistent warps over its polyphase items (an image's items
+// contiguous, plane-major), the image found by a binary search, the summed
+// taps recomputed when the (image, plane) changes.
+constexpr int kUp3RagWarps = 8;
+
+template <typename T>
+__global__ void __launch_bounds__(kUp3RagWarps * 32, 2) up3_rag_kernel(UpRagParams p, int n_items) {
+  float wt[36];
+  int img_cur = -1;
+  uint32_t plane_cur = 0;
+  for (int item = blockIdx.x * kUp3RagWarps + (threadIdx.x >> 5); item < n_items;
+       item += gridDim.x * kUp3RagWarps) {
+    const int tb = p.tile0 + item;
+    int lo = p.img_lo, hi = p.img_hi;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (p.images[mid].tile_base <= tb) lo = mid;
+      else hi = mid - 1;
+    }
+    const UpRagImage& im = p.images[lo];
+    const uint32_t t = (uint32_t)(tb - im.tile_base);
+    const uint32_t plane = fdiv(t, im.fpp);
+    const uint32_t r = t - plane * im.fpp.d;
+    const uint32_t rg = fdiv(r, im.fcb);
+    const int cb = (int)(r - rg * im.fcb.d);
+    if (lo != img_cur || plane != plane_cur) {
+      up3_weights<0>(im.w + (int64_t)plane * 9, wt);
+      img_cur = lo;
+      plane_cur = plane;
+    }
+    const int sc = (int)im.fs.d;
+    up3_item_mode<T>(im.mode, static_cast<const T*>(im.x) + (int64_t)plane * im.H * im.W,
+                     static_cast<T*>(im.y) + (int64_t)plane * im.Ho * im.Wo, im.H, im.W, sc,
+                     (int)rg * kUp3Rows, cb, p.clamp, wt);
+  }
 }
 
 }  // namespace giga
@@ -190,7 +227,14 @@ giga_status_t build_up_plan(const giga_up_image_t* images, int32_t n, int32_t bo
     r.Wo = (int)Wo;
     r.tiles_x = (int)((Wo + kTileW - 1) / kTileW);
     r.tiles_y = (int)((Ho + UpShape<1>::TH - 1) / UpShape<1>::TH);
-    const int64_t tiles = (int64_t)g.C * r.tiles_x * r.tiles_y;
+    int64_t tiles = (int64_t)g.C * r.tiles_x * r.tiles_y;
+    if (g.K == 3) {  // polyphase items: (plane, group of kUp3Rows rows, 32 columns)
+      const int64_t rgs = (g.H + kUp3Rows - 1) / kUp3Rows, cbs = ((int64_t)g.W + 31) / 32;
+      tiles = (int64_t)g.C * rgs * cbs;
+      r.mode = up3_mode(g.scale, g.y, (int)es);
+      r.fcb = make_fastdiv((uint32_t)cbs);
+      r.fpp = make_fastdiv((uint32_t)(rgs * cbs));
+    }
     if (tiles >= (1LL << 31)) return fail(GIGA_ERR_INVALID_ARG, where + "too many tiles");
     r.n_tiles = (int)tiles;
     const uintptr_t va = dtype == GIGA_F32 ? 16 : 8;
@@ -240,13 +284,28 @@ template <typename T, int K>
 cudaError_t up_rag_launch_k(const UpRagParams& p, int n_tiles, cudaStream_t st) {
   const size_t smem = (size_t)UpShape<K>::SM_FLOATS_1 * 4;
   cudaError_t e;
-  if constexpr (sizeof(T) == 4 && K == 3) {
-    if ((e = set_smem_once<up_rag_kernel_hi_occ<T, K>>(smem)) != cudaSuccess) return e;
-    up_rag_kernel_hi_occ<T, K><<<n_tiles, kThreads, smem, st>>>(p);
-  } else {
-    if ((e = set_smem_once<up_rag_kernel<T, K>>(smem)) != cudaSuccess) return e;
-    up_rag_kernel<T, K><<<n_tiles, kThreads, smem, st>>>(p);
+  if ((e = set_smem_once<up_rag_kernel<T, K>>(smem)) != cudaSuccess) return e;
+  up_rag_kernel<T, K><<<n_tiles, kThreads, smem, st>>>(p);
+  note_launch();
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t up3_rag_launch(const UpRagParams& p, int n_items, cudaStream_t st) {
+  static int ctas_per_sm[64] = {};  // per device, measured at its first launch
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int& per_sm = ctas_per_sm[dev & 63];
+  if (per_sm == 0) {
+    int n = 0;
+    cudaError_t e =
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, up3_rag_kernel<T>, kUp3RagWarps * 32, 0);
+    if (e != cudaSuccess) return e;
+    per_sm = n > 0 ? n : 1;
   }
+  const int grid = (int)std::min<int64_t>((n_items + kUp3RagWarps - 1) / kUp3RagWarps,
+                                          (int64_t)per_sm * sm_count());
+  up3_rag_kernel<T><<<grid, kUp3RagWarps * 32, 0, st>>>(p, n_items);
   note_launch();
   return cudaGetLastError();
 }
@@ -255,7 +314,7 @@ template <typename T>
 cudaError_t up_rag_launch(int K, const UpRagParams& p, int n_tiles, cudaStream_t st) {
   switch (K) {
     case 1: return up_rag_launch_k<T, 1>(p, n_tiles, st);
-    case 3: return up_rag_launch_k<T, 3>(p, n_tiles, st);
+    case 3: return up3_rag_launch<T>(p, n_tiles, st);
     case 5: return up_rag_launch_k<T, 5>(p, n_tiles, st);
     case 7: return up_rag_launch_k<T, 7>(p, n_tiles, st);
     case 9: return up_rag_launch_k<T, 9>(p, n_tiles, st);

@@ -55,112 +55,18 @@ __global__ void __launch_bounds__(256) up_nearest_kernel(const T* __restrict__ x
   }
 }
 
-// ------------------------- upsample, then the 3 x 3 filter: polyphase form
-// For K = 3 and s >= 2 the window of output pixel (s I + u, s J + v) covers
-// the upsampled rows s I + u - 1 .. s I + u + 1, which are input rows I - 1
-// and I when u = 0, row I alone when 0 < u < s - 1, rows I and I + 1 when
-// u = s - 1 (columns likewise).  So
-//   y[s I + u][s J + v] = sum_{i,j} Wt[R][C][i][j] * x~[I + o(R, i)][J + o(C, j)]
-// with row class R = R(u) in {top, middle, bottom}, column class C = C(v) in
-// {left, middle, right}, at most two input offsets o per class, and Wt the sum
-// of the taps that land on the same input pixel: 1, 2 or 4 multiply-adds per
-// output pixel instead of 9, no expanded rows, and all middle columns of a
-// class row equal.  The border rule applies to x~ directly: floor(P / s)
-// leaves [0, H) exactly when P leaves [0, H s), and the nearest upsampled
-// pixel of a clamped row is that of the nearest input row.  Rounding differs
-// from filtering the stored upsampled image (the taps of one input pixel are
-// added before the multiply); the FP32 error stays within gamma(K^2 + 4) of
-// the sum of |terms|.
-//
-// One warp: 32 consecutive input columns x kUp3Rows input rows, a 3 x 3
-// register window sliding down the rows (side neighbours by warp shuffle); a
-// CTA: kUp3Warps warps stacked vertically.  Each lane writes the s x s output
-// block of its input pixel, row by row, with CE-element vector stores
-// (s % CE == 0 and y aligned to CE elements).
-constexpr int kUp3Rows = 8;
+// Persistent warps, each on its own sequence of items (plane, group of
+// kUp3Rows input rows, block of 32 input columns; the column block fastest),
+// the summed taps recomputed when the channel changes.
 constexpr int kUp3Warps = 8;
-
-// Class R (0: top / left, 1: middle, 2: bottom / right): the taps (bit a:
-// tap a) that land on its input offset slot i, and that offset.
-__host__ __device__ constexpr int up3_taps(int R, int i) {
-  return R == 0 ? (i == 0 ? 1 : 6) : R == 1 ? (i == 0 ? 7 : 0) : (i == 0 ? 3 : 4);
-}
-__host__ __device__ constexpr int up3_off(int R, int i) {
-  return R == 0 ? (i == 0 ? -1 : 0) : R == 1 ? 0 : (i == 0 ? 0 : 1);
-}
-
-template <typename T, int CE> struct Up3Store;
-// 32-byte stores (sm_100 and later): one lane writes a whole sector.
-__device__ __forceinline__ void st_global_v8(void* p, uint32_t a0, uint32_t a1, uint32_t a2,
-                                             uint32_t a3, uint32_t a4, uint32_t a5, uint32_t a6,
-                                             uint32_t a7) {
-  asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "r"(a0),
-               "r"(a1), "r"(a2), "r"(a3), "r"(a4), "r"(a5), "r"(a6), "r"(a7)
-               : "memory");
-}
-
-template <int CE> struct Up3Store<float, CE> {
-  static __device__ __forceinline__ void put(float* p, const float (&e)[CE]) {
-    if constexpr (CE == 8)
-      st_global_v8(p, __float_as_uint(e[0]), __float_as_uint(e[1]), __float_as_uint(e[2]),
-                   __float_as_uint(e[3]), __float_as_uint(e[4]), __float_as_uint(e[5]),
-                   __float_as_uint(e[6]), __float_as_uint(e[7]));
-    else if constexpr (CE == 4) *reinterpret_cast<float4*>(p) = make_float4(e[0], e[1], e[2], e[3]);
-    else if constexpr (CE == 2) *reinterpret_cast<float2*>(p) = make_float2(e[0], e[1]);
-    else *p = e[0];
-  }
-};
-template <int CE> struct Up3Store<__nv_bfloat16, CE> {
-  static __device__ __forceinline__ uint32_t pack(float a, float b) {
-    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
-    return *reinterpret_cast<uint32_t*>(&h);
-  }
-  static __device__ __forceinline__ void put(__nv_bfloat16* p, const float (&e)[CE]) {
-    if constexpr (CE == 16)
-      st_global_v8(p, pack(e[0], e[1]), pack(e[2], e[3]), pack(e[4], e[5]), pack(e[6], e[7]),
-                   pack(e[8], e[9]), pack(e[10], e[11]), pack(e[12], e[13]), pack(e[14], e[15]));
-    else if constexpr (CE == 8)
-      *reinterpret_cast<uint4*>(p) =
-          make_uint4(pack(e[0], e[1]), pack(e[2], e[3]), pack(e[4], e[5]), pack(e[6], e[7]));
-    else if constexpr (CE == 4)
-      *reinterpret_cast<uint2*>(p) = make_uint2(pack(e[0], e[1]), pack(e[2], e[3]));
-    else if constexpr (CE == 2)
-      *reinterpret_cast<uint32_t*>(p) = pack(e[0], e[1]);
-    else
-      *p = __float2bfloat16_rn(e[0]);
-  }
-};
-
-// One output row of an input pixel's block: vl, then s - 2 times vm, then vr
-// (S: s when known at compile time, else 0).
-template <typename T, int CE, int S>
-__device__ __forceinline__ void up3_row(T* dst, int s, float vl, float vm, float vr) {
-  const int n = S ? S : s;
-#pragma unroll
-  for (int v0 = 0; v0 < (S ? S : n); v0 += CE) {
-    float e[CE];
-#pragma unroll
-    for (int k = 0; k < CE; ++k) {
-      const int v = v0 + k;
-      e[k] = v == 0 ? vl : (v == n - 1 ? vr : vm);
-    }
-    Up3Store<T, CE>::put(dst + v0, e);
-  }
-}
 
 template <typename T, int CE, int S>
 __global__ void __launch_bounds__(kUp3Warps * 32) up3_poly_kernel(
     const T* __restrict__ x, const float* __restrict__ w, T* __restrict__ y, FastDiv fc, int H,
     int W, int s, FastDiv fcb, FastDiv frb, uint32_t items, int clamp) {
-  if (S) s = S;  // the scale, a compile-time constant for S != 0
-  const int lane = threadIdx.x & 31;
-  const int64_t Wo = (int64_t)W * s;
-  // s = 2 has no middle row or column class
-  auto used = [](int R) { return S != 2 || R != 1; };
-  float wt[36];  // Wt[R][C][i][j] of channel c_cur
+  if (S) s = S;
+  float wt[36];
   int c_cur = -1;
-  // every warp on its own: items (plane, group of kUp3Rows input rows, block of
-  // 32 input columns), the column block fastest
   for (uint32_t item = blockIdx.x * kUp3Warps + (threadIdx.x >> 5); item < items;
        item += gridDim.x * kUp3Warps) {
     const uint32_t q = fdiv(item, fcb);
@@ -168,102 +74,12 @@ __global__ void __launch_bounds__(kUp3Warps * 32) up3_poly_kernel(
     const uint32_t plane = fdiv(q, frb);
     const int rg = (int)(q - plane * frb.d);
     const int c = (int)(plane - fdiv(plane, fc) * fc.d);
-    const int i0 = rg * kUp3Rows;
-    const int J = cb * 32 + lane;
-    const T* xp = x + (int64_t)plane * H * W;
-    // x~ with the border rule
-    auto ld = [&](int r, int col) -> float {
-      if (clamp) {
-        r = min(max(r, 0), H - 1);
-        col = min(max(col, 0), W - 1);
-      } else if (r < 0 || r >= H || col < 0 || col >= W) {
-        return 0.f;
-      }
-      return Elem<T>::load(xp + (int64_t)r * W + col);
-    };
-    // Columns J - 1, J, J + 1 of every input row the item needs (its rows and
-    // the halo above and below), all loads issued before the first use.
-    // Lanes past W hold the border value of their column, which is what
-    // their left neighbour needs.
-    constexpr int NR = kUp3Rows + 2;
-    const int side_col = lane == 0 ? J - 1 : J + 1;  // the neighbour outside the warp
-    float cm[NR], cs[NR];
-#pragma unroll
-    for (int k = 0; k < NR; ++k) {
-      cm[k] = ld(i0 - 1 + k, J);
-      cs[k] = (lane == 0 || lane == 31) ? ld(i0 - 1 + k, side_col) : 0.f;
-    }
-    if (c != c_cur) {  // the summed taps of this channel
-      float tap[9];
-#pragma unroll
-      for (int k = 0; k < 9; ++k) tap[k] = __ldg(w + (int64_t)c * 9 + k);
-#pragma unroll
-      for (int R = 0; R < 3; ++R)
-#pragma unroll
-        for (int C = 0; C < 3; ++C)
-#pragma unroll
-          for (int i = 0; i < 2; ++i)
-#pragma unroll
-            for (int j = 0; j < 2; ++j) {
-              if (!used(R) || !used(C)) continue;
-              float sum = 0.f;
-#pragma unroll
-              for (int a2 = 0; a2 < 3; ++a2)
-#pragma unroll
-                for (int b2 = 0; b2 < 3; ++b2)
-                  if ((up3_taps(R, i) >> a2 & 1) && (up3_taps(C, j) >> b2 & 1))
-                    sum += tap[a2 * 3 + b2];
-              wt[((R * 3 + C) * 2 + i) * 2 + j] = sum;
-            }
+    if (c != c_cur) {
+      up3_weights<S>(w + (int64_t)c * 9, wt);
       c_cur = c;
     }
-    float cl[NR], cr[NR];
-#pragma unroll
-    for (int k = 0; k < NR; ++k) {
-      const float up = __shfl_up_sync(0xffffffffu, cm[k], 1);
-      const float dn = __shfl_down_sync(0xffffffffu, cm[k], 1);
-      cl[k] = lane == 0 ? cs[k] : up;
-      cr[k] = lane == 31 ? cs[k] : dn;
-    }
-    // the output block of input pixel (i0, J), then one block row down per row
-    T* o = y + ((int64_t)plane * H + i0) * s * Wo + (int64_t)J * s;
-#pragma unroll
-    for (int k = 0; k < kUp3Rows; ++k, o += s * Wo) {
-      if (i0 + k >= H) break;
-      const float n[3][3] = {{cl[k], cm[k], cr[k]},
-                             {cl[k + 1], cm[k + 1], cr[k + 1]},
-                             {cl[k + 2], cm[k + 2], cr[k + 2]}};
-      float v[3][3];
-#pragma unroll
-      for (int R = 0; R < 3; ++R)
-#pragma unroll
-        for (int C = 0; C < 3; ++C) {
-          float acc = 0.f;
-          bool started = false;
-          if (!used(R) || !used(C)) {
-            v[R][C] = 0.f;
-            continue;
-          }
-#pragma unroll
-          for (int i = 0; i < 2; ++i)
-#pragma unroll
-            for (int j = 0; j < 2; ++j) {
-              if (up3_taps(R, i) == 0 || up3_taps(C, j) == 0) continue;
-              const float t = wt[((R * 3 + C) * 2 + i) * 2 + j];
-              const float xv = n[1 + up3_off(R, i)][1 + up3_off(C, j)];
-              acc = started ? fmaf(t, xv, acc) : t * xv;
-              started = true;
-            }
-          v[R][C] = acc;
-        }
-      if (J < W) {
-        up3_row<T, CE, S>(o, s, v[0][0], v[0][1], v[0][2]);
-#pragma unroll
-        for (int u = 1; u < (S ? S - 1 : s - 1); ++u)
-          up3_row<T, CE, S>(o + u * Wo, s, v[1][0], v[1][1], v[1][2]);
-        up3_row<T, CE, S>(o + (s - 1) * Wo, s, v[2][0], v[2][1], v[2][2]);
-      }
-    }
+    up3_item<T, CE, S>(x + (int64_t)plane * H * W, y + (int64_t)plane * H * s * ((int64_t)W * s),
+                       H, W, s, rg * kUp3Rows, cb, clamp, wt);
   }
 }
 
@@ -415,22 +231,22 @@ static cudaError_t up3_launch_ce(const UpArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-// K = 3: the polyphase kernel with the widest stores that s and y's alignment
-// allow (at most 32 bytes: one sector per lane); scales 2, 4 and 8 compiled
-// for their value (the class loops and stores unrolled), others at run time.
+// K = 3: the polyphase kernel compiled for the mode up3_mode picks.
 template <typename T>
 static cudaError_t up3_launch(const UpArgs& a, cudaStream_t st) {
-  const uintptr_t yp = reinterpret_cast<uintptr_t>(a.y);
-  auto fits = [&](int ce) { return a.s % ce == 0 && yp % (ce * sizeof(T)) == 0; };
-  constexpr int kSector = 32 / (int)sizeof(T);  // elements per 32-byte store
-  if (a.s == 2 && fits(2)) return up3_launch_ce<T, 2, 2>(a, st);
-  if (a.s == 4 && fits(4)) return up3_launch_ce<T, 4, 4>(a, st);
-  if (a.s == 8 && fits(8)) return up3_launch_ce<T, 8, 8>(a, st);
-  if (fits(kSector)) return up3_launch_ce<T, kSector, 0>(a, st);
-  if (fits(8) && 8 < kSector) return up3_launch_ce<T, 8, 0>(a, st);
-  if (fits(4)) return up3_launch_ce<T, 4, 0>(a, st);
-  if (fits(2)) return up3_launch_ce<T, 2, 0>(a, st);
-  return up3_launch_ce<T, 1, 0>(a, st);
+  constexpr int kSector = 32 / (int)sizeof(T);
+  switch (up3_mode(a.s, a.y, (int)sizeof(T))) {
+    case 0: return up3_launch_ce<T, 2, 2>(a, st);
+    case 1: return up3_launch_ce<T, 4, 4>(a, st);
+    case 2: return up3_launch_ce<T, 8, 8>(a, st);
+    case 3: return up3_launch_ce<T, kSector, 0>(a, st);
+    case 4:
+      if constexpr (sizeof(T) == 2) return up3_launch_ce<T, 8, 0>(a, st);
+      return cudaErrorInvalidValue;
+    case 5: return up3_launch_ce<T, 4, 0>(a, st);
+    case 6: return up3_launch_ce<T, 2, 0>(a, st);
+    default: return up3_launch_ce<T, 1, 0>(a, st);
+  }
 }
 
 template <typename T>

@@ -1,6 +1,7 @@
 // upsample.cuh -- pieces shared by the single-image and the batched
-// upsample-then-filter kernels (upsample.cu, up_batched.cu): fixed-divisor
-// division, the tile geometry and the per-tile body.
+// upsample-then-filter kernels (upsample.cu, up_batched.cu): the tile
+// geometry and per-tile body of the general K x K pass, and the polyphase
+// body of the 3 x 3 pass.
 //
 //   up[p][q] = x[p / s][q / s]                                   (integer division)
 //   y[p][q]  = sum_{a,b} w[a][b] * up~[p + a - r][q + b - r]     (GigaAPI paper,
@@ -196,6 +197,247 @@ __device__ __forceinline__ void up_tile(float* __restrict__ sx, int zero_off,
   fwd_block_tab<K, PY>(sx + 4 * lane, rowoff + warp * PY, sw, acc);
   store_block<T, PY>(yplane, Ho, Wo, ty0 + warp * PY, tx0 + 4 * lane, vec, acc);
   cta_barrier();  // the expanded rows, tables and the staged pixels are free again
+}
+
+// ------------------------- upsample, then the 3 x 3 filter: polyphase form
+// For K = 3 and s >= 2 the window of output pixel (s I + u, s J + v) covers
+// the upsampled rows s I + u - 1 .. s I + u + 1, which are input rows I - 1
+// and I when u = 0, row I alone when 0 < u < s - 1, rows I and I + 1 when
+// u = s - 1 (columns likewise).  So
+//   y[s I + u][s J + v] = sum_{i,j} Wt[R][C][i][j] * x~[I + o(R, i)][J + o(C, j)]
+// with row class R = R(u) in {top, middle, bottom}, column class C = C(v) in
+// {left, middle, right}, at most two input offsets o per class, and Wt the sum
+// of the taps that land on the same input pixel: 1, 2 or 4 multiply-adds per
+// output pixel instead of 9, no expanded rows, and all middle columns of a
+// class row equal.  The border rule applies to x~ directly: floor(P / s)
+// leaves [0, H) exactly when P leaves [0, H s), and the nearest upsampled
+// pixel of a clamped row is that of the nearest input row.  Rounding differs
+// from filtering the stored upsampled image (the taps of one input pixel are
+// added before the multiply); the FP32 error stays within gamma(K^2 + 4) of
+// the sum of |terms|.
+//
+// One item, one warp: 32 consecutive input columns x kUp3Rows input rows of one
+// plane, a 3 x 3 register window over the rows (side neighbours by warp
+// shuffle).  Each lane writes the s x s output block of its input pixel, row
+// by row, with CE-element vector stores (s % CE == 0 and y aligned to CE
+// elements).  S is s when compiled for one scale (2, 4, 8), else 0.
+constexpr int kUp3Rows = 8;
+
+// Class R (0: top / left, 1: middle, 2: bottom / right): the taps (bit a:
+// tap a) that land on its input offset slot i, and that offset.
+__host__ __device__ constexpr int up3_taps(int R, int i) {
+  return R == 0 ? (i == 0 ? 1 : 6) : R == 1 ? (i == 0 ? 7 : 0) : (i == 0 ? 3 : 4);
+}
+__host__ __device__ constexpr int up3_off(int R, int i) {
+  return R == 0 ? (i == 0 ? -1 : 0) : R == 1 ? 0 : (i == 0 ? 0 : 1);
+}
+
+template <typename T, int CE> struct Up3Store;
+// 32-byte stores (sm_100 and later): one lane writes a whole sector.
+__device__ __forceinline__ void st_global_v8(void* p, uint32_t a0, uint32_t a1, uint32_t a2,
+                                             uint32_t a3, uint32_t a4, uint32_t a5, uint32_t a6,
+                                             uint32_t a7) {
+  asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "r"(a0),
+               "r"(a1), "r"(a2), "r"(a3), "r"(a4), "r"(a5), "r"(a6), "r"(a7)
+               : "memory");
+}
+
+template <int CE> struct Up3Store<float, CE> {
+  static __device__ __forceinline__ void put(float* p, const float (&e)[CE]) {
+    if constexpr (CE == 8)
+      st_global_v8(p, __float_as_uint(e[0]), __float_as_uint(e[1]), __float_as_uint(e[2]),
+                   __float_as_uint(e[3]), __float_as_uint(e[4]), __float_as_uint(e[5]),
+                   __float_as_uint(e[6]), __float_as_uint(e[7]));
+    else if constexpr (CE == 4) *reinterpret_cast<float4*>(p) = make_float4(e[0], e[1], e[2], e[3]);
+    else if constexpr (CE == 2) *reinterpret_cast<float2*>(p) = make_float2(e[0], e[1]);
+    else *p = e[0];
+  }
+};
+template <int CE> struct Up3Store<__nv_bfloat16, CE> {
+  static __device__ __forceinline__ uint32_t pack(float a, float b) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t*>(&h);
+  }
+  static __device__ __forceinline__ void put(__nv_bfloat16* p, const float (&e)[CE]) {
+    if constexpr (CE == 16)
+      st_global_v8(p, pack(e[0], e[1]), pack(e[2], e[3]), pack(e[4], e[5]), pack(e[6], e[7]),
+                   pack(e[8], e[9]), pack(e[10], e[11]), pack(e[12], e[13]), pack(e[14], e[15]));
+    else if constexpr (CE == 8)
+      *reinterpret_cast<uint4*>(p) =
+          make_uint4(pack(e[0], e[1]), pack(e[2], e[3]), pack(e[4], e[5]), pack(e[6], e[7]));
+    else if constexpr (CE == 4)
+      *reinterpret_cast<uint2*>(p) = make_uint2(pack(e[0], e[1]), pack(e[2], e[3]));
+    else if constexpr (CE == 2)
+      *reinterpret_cast<uint32_t*>(p) = pack(e[0], e[1]);
+    else
+      *p = __float2bfloat16_rn(e[0]);
+  }
+};
+
+// One output row of an input pixel's block: vl, then s - 2 times vm, then vr
+// (S: s when known at compile time, else 0).
+template <typename T, int CE, int S>
+__device__ __forceinline__ void up3_row(T* dst, int s, float vl, float vm, float vr) {
+  const int n = S ? S : s;
+#pragma unroll
+  for (int v0 = 0; v0 < (S ? S : n); v0 += CE) {
+    float e[CE];
+#pragma unroll
+    for (int k = 0; k < CE; ++k) {
+      const int v = v0 + k;
+      e[k] = v == 0 ? vl : (v == n - 1 ? vr : vm);
+    }
+    Up3Store<T, CE>::put(dst + v0, e);
+  }
+}
+
+// s = 2 has no middle row or column class.
+template <int S>
+__host__ __device__ constexpr bool up3_used(int R) { return S != 2 || R != 1; }
+
+// Wt[R][C][i][j] of one channel (wc: its 3 x 3 taps): the taps of the row
+// slot i of class R and the column slot j of class C, summed row-major.
+template <int S>
+__device__ __forceinline__ void up3_weights(const float* __restrict__ wc, float (&wt)[36]) {
+  float tap[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) tap[k] = __ldg(wc + k);
+#pragma unroll
+  for (int R = 0; R < 3; ++R)
+#pragma unroll
+    for (int C = 0; C < 3; ++C)
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          float sum = 0.f;
+          if (up3_used<S>(R) && up3_used<S>(C)) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+              for (int b = 0; b < 3; ++b)
+                if ((up3_taps(R, i) >> a & 1) && (up3_taps(C, j) >> b & 1)) sum += tap[a * 3 + b];
+          }
+          wt[((R * 3 + C) * 2 + i) * 2 + j] = sum;
+        }
+}
+
+// One item: input rows i0 .. i0 + kUp3Rows - 1 (those below H) and columns
+// 32 cb .. 32 cb + 31 of the plane xp (H x W), output plane yp (H s x W s).
+// Every lane of the warp calls it.
+template <typename T, int CE, int S>
+__device__ __forceinline__ void up3_item(const T* __restrict__ xp, T* __restrict__ yp, int H,
+                                         int W, int s, int i0, int cb, int clamp,
+                                         const float (&wt)[36]) {
+  if (S) s = S;
+  const int lane = threadIdx.x & 31;
+  const int J = cb * 32 + lane;
+  const int64_t Wo = (int64_t)W * s;
+  // x~ with the border rule
+  auto ld = [&](int r, int col) -> float {
+    if (clamp) {
+      r = min(max(r, 0), H - 1);
+      col = min(max(col, 0), W - 1);
+    } else if (r < 0 || r >= H || col < 0 || col >= W) {
+      return 0.f;
+    }
+    return Elem<T>::load(xp + (int64_t)r * W + col);
+  };
+  // Columns J - 1, J, J + 1 of every input row the item needs (its rows and
+  // the halo above and below), all loads issued before the first use.  Lanes
+  // past W hold the border value of their column, which is what their left
+  // neighbour needs.
+  constexpr int NR = kUp3Rows + 2;
+  const int side_col = lane == 0 ? J - 1 : J + 1;  // the neighbour outside the warp
+  float cm[NR], cs[NR];
+#pragma unroll
+  for (int k = 0; k < NR; ++k) {
+    cm[k] = ld(i0 - 1 + k, J);
+    cs[k] = (lane == 0 || lane == 31) ? ld(i0 - 1 + k, side_col) : 0.f;
+  }
+  float cl[NR], cr[NR];
+#pragma unroll
+  for (int k = 0; k < NR; ++k) {
+    const float up = __shfl_up_sync(0xffffffffu, cm[k], 1);
+    const float dn = __shfl_down_sync(0xffffffffu, cm[k], 1);
+    cl[k] = lane == 0 ? cs[k] : up;
+    cr[k] = lane == 31 ? cs[k] : dn;
+  }
+  // the output block of input pixel (i0, J), then one block row down per row
+  T* o = yp + (int64_t)i0 * s * Wo + (int64_t)J * s;
+#pragma unroll
+  for (int k = 0; k < kUp3Rows; ++k, o += s * Wo) {
+    if (i0 + k >= H) break;
+    const float n[3][3] = {{cl[k], cm[k], cr[k]},
+                           {cl[k + 1], cm[k + 1], cr[k + 1]},
+                           {cl[k + 2], cm[k + 2], cr[k + 2]}};
+    float v[3][3];
+#pragma unroll
+    for (int R = 0; R < 3; ++R)
+#pragma unroll
+      for (int C = 0; C < 3; ++C) {
+        float acc = 0.f;
+        bool started = false;
+        if (up3_used<S>(R) && up3_used<S>(C)) {
+#pragma unroll
+          for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+              if (up3_taps(R, i) == 0 || up3_taps(C, j) == 0) continue;
+              const float t = wt[((R * 3 + C) * 2 + i) * 2 + j];
+              const float xv = n[1 + up3_off(R, i)][1 + up3_off(C, j)];
+              acc = started ? fmaf(t, xv, acc) : t * xv;
+              started = true;
+            }
+        }
+        v[R][C] = acc;
+      }
+    if (J < W) {
+      up3_row<T, CE, S>(o, s, v[0][0], v[0][1], v[0][2]);
+#pragma unroll
+      for (int u = 1; u < (S ? S - 1 : s - 1); ++u)
+        up3_row<T, CE, S>(o + u * Wo, s, v[1][0], v[1][1], v[1][2]);
+      up3_row<T, CE, S>(o + (s - 1) * Wo, s, v[2][0], v[2][1], v[2][2]);
+    }
+  }
+}
+
+// The compilation of the polyphase body for scale s and output address y:
+// s itself where compiled for it (2, 4, 8), else run-time s, with the widest
+// stores s and y's alignment allow (at most 32 bytes).  Modes 0-2: (CE, S) =
+// (2, 2), (4, 4), (8, 8); 3: one 32-byte sector, run-time s; 4: 8 elements
+// (BF16 only); 5: 4; 6: 2; 7: 1.
+inline int up3_mode(int s, const void* y, int elem_bytes) {
+  const uintptr_t yp = reinterpret_cast<uintptr_t>(y);
+  auto fits = [&](int ce) { return s % ce == 0 && yp % (uintptr_t)(ce * elem_bytes) == 0; };
+  if (s == 2 && fits(2)) return 0;
+  if (s == 4 && fits(4)) return 1;
+  if (s == 8 && fits(8)) return 2;
+  if (fits(32 / elem_bytes)) return 3;
+  if (elem_bytes == 2 && fits(8)) return 4;
+  if (fits(4)) return 5;
+  if (fits(2)) return 6;
+  return 7;
+}
+
+// The body of mode m (a warp-uniform switch).
+template <typename T>
+__device__ __forceinline__ void up3_item_mode(int m, const T* __restrict__ xp, T* __restrict__ yp,
+                                              int H, int W, int s, int i0, int cb, int clamp,
+                                              const float (&wt)[36]) {
+  constexpr int kSector = 32 / (int)sizeof(T);
+  switch (m) {
+    case 0: up3_item<T, 2, 2>(xp, yp, H, W, s, i0, cb, clamp, wt); break;
+    case 1: up3_item<T, 4, 4>(xp, yp, H, W, s, i0, cb, clamp, wt); break;
+    case 2: up3_item<T, 8, 8>(xp, yp, H, W, s, i0, cb, clamp, wt); break;
+    case 3: up3_item<T, kSector, 0>(xp, yp, H, W, s, i0, cb, clamp, wt); break;
+    case 4:
+      if constexpr (sizeof(T) == 2) up3_item<T, 8, 0>(xp, yp, H, W, s, i0, cb, clamp, wt);
+      break;
+    case 5: up3_item<T, 4, 0>(xp, yp, H, W, s, i0, cb, clamp, wt); break;
+    case 6: up3_item<T, 2, 0>(xp, yp, H, W, s, i0, cb, clamp, wt); break;
+    default: up3_item<T, 1, 0>(xp, yp, H, W, s, i0, cb, clamp, wt); break;
+  }
 }
 
 }  // namespace giga
