@@ -170,6 +170,7 @@ constexpr int kAccBufs = 8;                            // TMEM accumulators (64 
 constexpr int kOutBufs = 2;                            // output staging tiles (16 KB each)
 constexpr size_t kDenseSmemBand = 1024 + kDenseTaps * kDenseBBytes + kBandSlots * kSlotBytes +
                                   kOutBufs * kDenseABytes + 256;
+static_assert((2 * kBandSlots + 2 + 2 * kAccBufs) * 8 + 4 <= 256, "barrier area");
 
 __device__ __forceinline__ void tile_range(int64_t total, int64_t& begin, int64_t& end) {
   begin = total * blockIdx.x / gridDim.x;
@@ -204,7 +205,8 @@ __global__ void __launch_bounds__(kDenseThreads, 1)
   uint64_t* bfull = bars + 2 * kBandSlots;
   uint64_t* tfull = bars + 2 * kBandSlots + 1;              // [kAccBufs]
   uint64_t* tempty = bars + 2 * kBandSlots + 1 + kAccBufs;  // [kAccBufs]
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kBandSlots + 1 + 2 * kAccBufs);
+  uint64_t* drain = bars + 2 * kBandSlots + 1 + 2 * kAccBufs;  // the issuer's MMAs are done
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
   __shared__ volatile int s_abort;
   __shared__ volatile int s_go;
 
@@ -223,6 +225,7 @@ __global__ void __launch_bounds__(kDenseThreads, 1)
       mbar_init(tfull + a, 1);
       mbar_init(tempty + a, 4 * 32);
     }
+    mbar_init(drain, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
@@ -265,6 +268,14 @@ __global__ void __launch_bounds__(kDenseThreads, 1)
           tma_load_4d(sA + slot * kSlotBytes, &tmap_x, 0, jt * kDenseTileM - 1, r, n, full + slot);
         }
         tile = run_end;
+      }
+      if (s_abort) {
+        // let the loads still in flight land (bounded) before the CTA exits:
+        // the weights and at most the last kBandSlots bands (an older band's
+        // slot was refilled only after that band had arrived and been used)
+        mbar_wait(bfull, 0);
+        for (uint32_t q = seq > (uint32_t)kBandSlots ? seq - kBandSlots : 0; q < seq; ++q)
+          mbar_wait(full + q % kBandSlots, (q / kBandSlots) & 1);
       }
     }
   } else if (warp == 1) {
@@ -331,6 +342,10 @@ __global__ void __launch_bounds__(kDenseThreads, 1)
         o_base += rows;
         tile = run_end;
       }
+      // every MMA issued above has completed before the CTA frees TMEM (at
+      // once on the normal path, where the epilogue has waited for each row)
+      tc_commit(drain);
+      mbar_wait(drain, 0);
     }
   } else {
     // ------------------------------------------------------------ epilogue
@@ -562,6 +577,14 @@ __global__ void __launch_bounds__(kDenseThreads, 1)
         }
         tile = run_end;
       }
+      if (s_abort) {
+        // let the loads still in flight land (bounded) before the CTA exits:
+        // at most the last kWgXSlots x bands and kWgDySlots dy bands
+        for (uint32_t q = xc > (uint32_t)kWgXSlots ? xc - kWgXSlots : 0; q < xc; ++q)
+          mbar_wait(xfull + q % kWgXSlots, (q / kWgXSlots) & 1);
+        for (uint32_t q = dc > (uint32_t)kWgDySlots ? dc - kWgDySlots : 0; q < dc; ++q)
+          mbar_wait(dyfull + q % kWgDySlots, (q / kWgDySlots) & 1);
+      }
     }
   } else if (warp == 1) {
     if (lane == 0) {
@@ -612,8 +635,9 @@ __global__ void __launch_bounds__(kDenseThreads, 1)
         dc += rows;
         tile = run_end;
       }
-      if (ok) tc_commit(done);  // fires once every MMA above has completed
-      else mbar_arrive(done);
+      // fires once every MMA issued above has completed (also after an abort,
+      // so the epilogue's wait covers them before TMEM is freed)
+      tc_commit(done);
     }
   } else {
     // epilogue: TMEM -> FP32 partials [tap][c][o] of this CTA.  TMEM lane
