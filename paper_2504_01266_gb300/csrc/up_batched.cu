@@ -18,7 +18,7 @@
 // allocation and its filter taps in uniform registers; a single kernel
 // switching on K per tile measured 125 registers instead of at most 72.  The
 // 3 x 3 class is numbered in the polyphase kernel's items instead (plane,
-// group of 8 input rows, 32 input columns) and run by persistent warps.  The
+// group of 8 input rows, 32 or 64 input columns) and run by persistent warps.  The
 // per-tile and per-item bodies are the single-image kernels' (upsample.cuh),
 // so every output equals that of giga_upsample_conv2d_fwd on the image alone,
 // bit for bit.
@@ -228,10 +228,11 @@ giga_status_t build_up_plan(const giga_up_image_t* images, int32_t n, int32_t bo
     r.tiles_x = (int)((Wo + kTileW - 1) / kTileW);
     r.tiles_y = (int)((Ho + UpShape<1>::TH - 1) / UpShape<1>::TH);
     int64_t tiles = (int64_t)g.C * r.tiles_x * r.tiles_y;
-    if (g.K == 3) {  // polyphase items: (plane, group of kUp3Rows rows, 32 columns)
-      const int64_t rgs = (g.H + kUp3Rows - 1) / kUp3Rows, cbs = ((int64_t)g.W + 31) / 32;
+    if (g.K == 3) {  // polyphase items: (plane, group of kUp3Rows rows, block of columns)
+      r.mode = up3_mode(g.scale, g.y, (int)es, g.W);
+      const int cols = up3_cols(r.mode);
+      const int64_t rgs = (g.H + kUp3Rows - 1) / kUp3Rows, cbs = ((int64_t)g.W + cols - 1) / cols;
       tiles = (int64_t)g.C * rgs * cbs;
-      r.mode = up3_mode(g.scale, g.y, (int)es);
       r.fcb = make_fastdiv((uint32_t)cbs);
       r.fpp = make_fastdiv((uint32_t)(rgs * cbs));
     }

@@ -56,11 +56,11 @@ __global__ void __launch_bounds__(256) up_nearest_kernel(const T* __restrict__ x
 }
 
 // Persistent warps, each on its own sequence of items (plane, group of
-// kUp3Rows input rows, block of 32 input columns; the column block fastest),
+// kUp3Rows input rows, block of 32 PX input columns; the column block fastest),
 // the summed taps recomputed when the channel changes.
 constexpr int kUp3Warps = 8;
 
-template <typename T, int CE, int S>
+template <typename T, int CE, int S, int PX>
 __global__ void __launch_bounds__(kUp3Warps * 32) up3_poly_kernel(
     const T* __restrict__ x, const float* __restrict__ w, T* __restrict__ y, FastDiv fc, int H,
     int W, int s, FastDiv fcb, FastDiv frb, uint32_t items, int clamp) {
@@ -78,8 +78,9 @@ __global__ void __launch_bounds__(kUp3Warps * 32) up3_poly_kernel(
       up3_weights<S>(w + (int64_t)c * 9, wt);
       c_cur = c;
     }
-    up3_item<T, CE, S>(x + (int64_t)plane * H * W, y + (int64_t)plane * H * s * ((int64_t)W * s),
-                       H, W, s, rg * kUp3Rows, cb, clamp, wt);
+    up3_item<T, CE, S, PX>(x + (int64_t)plane * H * W,
+                           y + (int64_t)plane * H * s * ((int64_t)W * s), H, W, s, rg * kUp3Rows,
+                           cb, clamp, wt);
   }
 }
 
@@ -204,10 +205,10 @@ static cudaError_t up_fwd_impl(const UpArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-template <typename T, int CE, int S>
+template <typename T, int CE, int S, int PX>
 static cudaError_t up3_launch_ce(const UpArgs& a, cudaStream_t st) {
   const int64_t rgs = (a.H + kUp3Rows - 1) / kUp3Rows;
-  const int64_t cbs = (a.W + 31) / 32;
+  const int64_t cbs = (a.W + 32 * PX - 1) / (32 * PX);
   const int64_t items = a.N * a.C * rgs * cbs;
   if (items > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
   static int ctas_per_sm[64] = {};  // per device, measured at its first launch
@@ -217,13 +218,13 @@ static cudaError_t up3_launch_ce(const UpArgs& a, cudaStream_t st) {
   if (per_sm == 0) {
     int n = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &n, up3_poly_kernel<T, CE, S>, kUp3Warps * 32, 0);
+        &n, up3_poly_kernel<T, CE, S, PX>, kUp3Warps * 32, 0);
     if (e != cudaSuccess) return e;
     per_sm = n > 0 ? n : 1;
   }
   const int64_t grid = std::min<int64_t>((items + kUp3Warps - 1) / kUp3Warps,
                                          (int64_t)per_sm * sm_count());
-  up3_poly_kernel<T, CE, S><<<(unsigned)grid, kUp3Warps * 32, 0, st>>>(
+  up3_poly_kernel<T, CE, S, PX><<<(unsigned)grid, kUp3Warps * 32, 0, st>>>(
       static_cast<const T*>(a.x), a.w, static_cast<T*>(a.y), make_fastdiv((uint32_t)a.C),
       (int)a.H, (int)a.W, a.s, make_fastdiv((uint32_t)cbs), make_fastdiv((uint32_t)rgs),
       (uint32_t)items, a.border);
@@ -235,17 +236,18 @@ static cudaError_t up3_launch_ce(const UpArgs& a, cudaStream_t st) {
 template <typename T>
 static cudaError_t up3_launch(const UpArgs& a, cudaStream_t st) {
   constexpr int kSector = 32 / (int)sizeof(T);
-  switch (up3_mode(a.s, a.y, (int)sizeof(T))) {
-    case 0: return up3_launch_ce<T, 2, 2>(a, st);
-    case 1: return up3_launch_ce<T, 4, 4>(a, st);
-    case 2: return up3_launch_ce<T, 8, 8>(a, st);
-    case 3: return up3_launch_ce<T, kSector, 0>(a, st);
-    case 4:
-      if constexpr (sizeof(T) == 2) return up3_launch_ce<T, 8, 0>(a, st);
+  switch (up3_mode(a.s, a.y, (int)sizeof(T), a.W)) {
+    case 0: return up3_launch_ce<T, 4, 2, 2>(a, st);
+    case 1: return up3_launch_ce<T, 2, 2, 1>(a, st);
+    case 2: return up3_launch_ce<T, 4, 4, 1>(a, st);
+    case 3: return up3_launch_ce<T, 8, 8, 1>(a, st);
+    case 4: return up3_launch_ce<T, kSector, 0, 1>(a, st);
+    case 5:
+      if constexpr (sizeof(T) == 2) return up3_launch_ce<T, 8, 0, 1>(a, st);
       return cudaErrorInvalidValue;
-    case 5: return up3_launch_ce<T, 4, 0>(a, st);
-    case 6: return up3_launch_ce<T, 2, 0>(a, st);
-    default: return up3_launch_ce<T, 1, 0>(a, st);
+    case 6: return up3_launch_ce<T, 4, 0, 1>(a, st);
+    case 7: return up3_launch_ce<T, 2, 0, 1>(a, st);
+    default: return up3_launch_ce<T, 1, 0, 1>(a, st);
   }
 }
 

@@ -274,20 +274,36 @@ template <int CE> struct Up3Store<__nv_bfloat16, CE> {
   }
 };
 
-// One output row of an input pixel's block: vl, then s - 2 times vm, then vr
-// (S: s when known at compile time, else 0).
-template <typename T, int CE, int S>
-__device__ __forceinline__ void up3_row(T* dst, int s, float vl, float vm, float vr) {
-  const int n = S ? S : s;
-#pragma unroll
-  for (int v0 = 0; v0 < (S ? S : n); v0 += CE) {
+// One output row of a lane's PX input pixels: for pixel p, vl[p], then s - 2
+// times vm[p], then vr[p] (S: s when known at compile time, else 0).  Either
+// CE = PX * S (one store for all pixels) or CE divides s; dst is aligned to
+// CE elements.
+template <typename T, int CE, int S, int PX>
+__device__ __forceinline__ void up3_row(T* dst, int s, const float (&vl)[PX],
+                                        const float (&vm)[PX], const float (&vr)[PX]) {
+  if constexpr (S != 0 && CE > S) {
+    static_assert(CE == PX * S, "one store covers every pixel of the lane");
     float e[CE];
 #pragma unroll
     for (int k = 0; k < CE; ++k) {
-      const int v = v0 + k;
-      e[k] = v == 0 ? vl : (v == n - 1 ? vr : vm);
+      const int q = k / S, v = k % S;
+      e[k] = v == 0 ? vl[q] : (v == S - 1 ? vr[q] : vm[q]);
     }
-    Up3Store<T, CE>::put(dst + v0, e);
+    Up3Store<T, CE>::put(dst, e);
+  } else {
+    const int n = S ? S : s;
+#pragma unroll
+    for (int p = 0; p < PX; ++p)
+#pragma unroll
+      for (int v0 = 0; v0 < (S ? S : n); v0 += CE) {
+        float e[CE];
+#pragma unroll
+        for (int k = 0; k < CE; ++k) {
+          const int v = v0 + k;
+          e[k] = v == 0 ? vl[p] : (v == n - 1 ? vr[p] : vm[p]);
+        }
+        Up3Store<T, CE>::put(dst + p * n + v0, e);
+      }
   }
 }
 
@@ -323,15 +339,16 @@ __device__ __forceinline__ void up3_weights(const float* __restrict__ wc, float 
 }
 
 // One item: input rows i0 .. i0 + kUp3Rows - 1 (those below H) and columns
-// 32 cb .. 32 cb + 31 of the plane xp (H x W), output plane yp (H s x W s).
-// Every lane of the warp calls it.
-template <typename T, int CE, int S>
+// 32 PX cb .. 32 PX cb + 32 PX - 1 (PX consecutive ones per lane) of the
+// plane xp (H x W), output plane yp (H s x W s).  Every lane of the warp calls
+// it.
+template <typename T, int CE, int S, int PX>
 __device__ __forceinline__ void up3_item(const T* __restrict__ xp, T* __restrict__ yp, int H,
                                          int W, int s, int i0, int cb, int clamp,
                                          const float (&wt)[36]) {
   if (S) s = S;
   const int lane = threadIdx.x & 31;
-  const int J = cb * 32 + lane;
+  const int J0 = (cb * 32 + lane) * PX;  // the lane's first input column
   const int64_t Wo = (int64_t)W * s;
   // x~ with the border rule
   auto ld = [&](int r, int col) -> float {
@@ -343,82 +360,107 @@ __device__ __forceinline__ void up3_item(const T* __restrict__ xp, T* __restrict
     }
     return Elem<T>::load(xp + (int64_t)r * W + col);
   };
-  // Columns J - 1, J, J + 1 of every input row the item needs (its rows and
+  // Columns J0 - 1 .. J0 + PX of every input row the item needs (its rows and
   // the halo above and below), all loads issued before the first use.  Lanes
-  // past W hold the border value of their column, which is what their left
+  // past W hold the border value of their columns, which is what their left
   // neighbour needs.
   constexpr int NR = kUp3Rows + 2;
-  const int side_col = lane == 0 ? J - 1 : J + 1;  // the neighbour outside the warp
-  float cm[NR], cs[NR];
+  const int side_col = lane == 0 ? J0 - 1 : J0 + PX;  // the neighbour outside the warp
+  float cm[NR][PX], cs[NR];
 #pragma unroll
   for (int k = 0; k < NR; ++k) {
-    cm[k] = ld(i0 - 1 + k, J);
+#pragma unroll
+    for (int p = 0; p < PX; ++p) cm[k][p] = ld(i0 - 1 + k, J0 + p);
     cs[k] = (lane == 0 || lane == 31) ? ld(i0 - 1 + k, side_col) : 0.f;
   }
   float cl[NR], cr[NR];
 #pragma unroll
   for (int k = 0; k < NR; ++k) {
-    const float up = __shfl_up_sync(0xffffffffu, cm[k], 1);
-    const float dn = __shfl_down_sync(0xffffffffu, cm[k], 1);
+    const float up = __shfl_up_sync(0xffffffffu, cm[k][PX - 1], 1);
+    const float dn = __shfl_down_sync(0xffffffffu, cm[k][0], 1);
     cl[k] = lane == 0 ? cs[k] : up;
     cr[k] = lane == 31 ? cs[k] : dn;
   }
-  // the output block of input pixel (i0, J), then one block row down per row
-  T* o = yp + (int64_t)i0 * s * Wo + (int64_t)J * s;
+  // column c of the lane's window: J0 - 1 + c, c in [0, PX + 2)
+  auto col = [&](int k, int c) { return c == 0 ? cl[k] : (c == PX + 1 ? cr[k] : cm[k][c - 1]); };
+  // the output blocks of input pixels (i0, J0 ..), then one block row down per row
+  T* o = yp + (int64_t)i0 * s * Wo + (int64_t)J0 * s;
 #pragma unroll
   for (int k = 0; k < kUp3Rows; ++k, o += s * Wo) {
     if (i0 + k >= H) break;
-    const float n[3][3] = {{cl[k], cm[k], cr[k]},
-                           {cl[k + 1], cm[k + 1], cr[k + 1]},
-                           {cl[k + 2], cm[k + 2], cr[k + 2]}};
-    float v[3][3];
+    float v[3][3][PX];
 #pragma unroll
-    for (int R = 0; R < 3; ++R)
+    for (int p = 0; p < PX; ++p) {
+      const float n[3][3] = {{col(k, p), col(k, p + 1), col(k, p + 2)},
+                             {col(k + 1, p), col(k + 1, p + 1), col(k + 1, p + 2)},
+                             {col(k + 2, p), col(k + 2, p + 1), col(k + 2, p + 2)}};
 #pragma unroll
-      for (int C = 0; C < 3; ++C) {
-        float acc = 0.f;
-        bool started = false;
-        if (up3_used<S>(R) && up3_used<S>(C)) {
+      for (int R = 0; R < 3; ++R)
 #pragma unroll
-          for (int i = 0; i < 2; ++i)
+        for (int C = 0; C < 3; ++C) {
+          float acc = 0.f;
+          bool started = false;
+          if (up3_used<S>(R) && up3_used<S>(C)) {
 #pragma unroll
-            for (int j = 0; j < 2; ++j) {
-              if (up3_taps(R, i) == 0 || up3_taps(C, j) == 0) continue;
-              const float t = wt[((R * 3 + C) * 2 + i) * 2 + j];
-              const float xv = n[1 + up3_off(R, i)][1 + up3_off(C, j)];
-              acc = started ? fmaf(t, xv, acc) : t * xv;
-              started = true;
-            }
+            for (int i = 0; i < 2; ++i)
+#pragma unroll
+              for (int j = 0; j < 2; ++j) {
+                if (up3_taps(R, i) == 0 || up3_taps(C, j) == 0) continue;
+                const float t = wt[((R * 3 + C) * 2 + i) * 2 + j];
+                const float xv = n[1 + up3_off(R, i)][1 + up3_off(C, j)];
+                acc = started ? fmaf(t, xv, acc) : t * xv;
+                started = true;
+              }
+          }
+          v[R][C][p] = acc;
         }
-        v[R][C] = acc;
-      }
-    if (J < W) {
-      up3_row<T, CE, S>(o, s, v[0][0], v[0][1], v[0][2]);
+    }
+    if (J0 + PX <= W) {
+      up3_row<T, CE, S, PX>(o, s, v[0][0], v[0][1], v[0][2]);
 #pragma unroll
       for (int u = 1; u < (S ? S - 1 : s - 1); ++u)
-        up3_row<T, CE, S>(o + u * Wo, s, v[1][0], v[1][1], v[1][2]);
-      up3_row<T, CE, S>(o + (s - 1) * Wo, s, v[2][0], v[2][1], v[2][2]);
+        up3_row<T, CE, S, PX>(o + u * Wo, s, v[1][0], v[1][1], v[1][2]);
+      up3_row<T, CE, S, PX>(o + (s - 1) * Wo, s, v[2][0], v[2][1], v[2][2]);
+    } else if constexpr (PX > 1) {
+      // the last pixels of a row: element stores for those inside the image
+#pragma unroll
+      for (int p = 0; p < PX; ++p) {
+        if (J0 + p >= W) break;
+        for (int u = 0; u < s; ++u) {
+          const int R = u == 0 ? 0 : (u == s - 1 ? 2 : 1);
+          for (int q = 0; q < s; ++q) {
+            const int C = q == 0 ? 0 : (q == s - 1 ? 2 : 1);
+            Elem<T>::store(o + u * Wo + p * s + q, v[R][C][p]);
+          }
+        }
+      }
     }
   }
 }
 
-// The compilation of the polyphase body for scale s and output address y:
-// s itself where compiled for it (2, 4, 8), else run-time s, with the widest
-// stores s and y's alignment allow (at most 32 bytes).  Modes 0-2: (CE, S) =
-// (2, 2), (4, 4), (8, 8); 3: one 32-byte sector, run-time s; 4: 8 elements
-// (BF16 only); 5: 4; 6: 2; 7: 1.
-inline int up3_mode(int s, const void* y, int elem_bytes) {
+// The compilation of the polyphase body for scale s, output address y and
+// input width W: s itself where compiled for it (2, 4, 8), else run-time s,
+// with the widest stores s, y's alignment and W allow (at most 32 bytes).
+// Mode 0: s = 2 with two input pixels per lane (one 4-element store per
+// output row; W even keeps every output row aligned); 1-3: (CE, S) = (2, 2),
+// (4, 4), (8, 8); 4: one 32-byte sector, run-time s; 5: 8 elements (BF16
+// only); 6: 4; 7: 2; 8: 1.
+inline int up3_mode(int s, const void* y, int elem_bytes, int64_t W) {
   const uintptr_t yp = reinterpret_cast<uintptr_t>(y);
   auto fits = [&](int ce) { return s % ce == 0 && yp % (uintptr_t)(ce * elem_bytes) == 0; };
-  if (s == 2 && fits(2)) return 0;
-  if (s == 4 && fits(4)) return 1;
-  if (s == 8 && fits(8)) return 2;
-  if (fits(32 / elem_bytes)) return 3;
-  if (elem_bytes == 2 && fits(8)) return 4;
-  if (fits(4)) return 5;
-  if (fits(2)) return 6;
-  return 7;
+  if (s == 2 && W % 2 == 0 && yp % (uintptr_t)(4 * elem_bytes) == 0) return 0;
+  if (s == 2 && fits(2)) return 1;
+  if (s == 4 && fits(4)) return 2;
+  if (s == 8 && fits(8)) return 3;
+  if (fits(32 / elem_bytes)) return 4;
+  if (elem_bytes == 2 && fits(8)) return 5;
+  if (fits(4)) return 6;
+  if (fits(2)) return 7;
+  return 8;
 }
+
+// Input columns per item of mode m.
+__host__ __device__ constexpr int up3_cols(int m) { return m == 0 ? 64 : 32; }
 
 // The body of mode m (a warp-uniform switch).
 template <typename T>
@@ -427,16 +469,17 @@ __device__ __forceinline__ void up3_item_mode(int m, const T* __restrict__ xp, T
                                               const float (&wt)[36]) {
   constexpr int kSector = 32 / (int)sizeof(T);
   switch (m) {
-    case 0: up3_item<T, 2, 2>(xp, yp, H, W, s, i0, cb, clamp, wt); break;
-    case 1: up3_item<T, 4, 4>(xp, yp, H, W, s, i0, cb, clamp, wt); break;
-    case 2: up3_item<T, 8, 8>(xp, yp, H, W, s, i0, cb, clamp, wt); break;
-    case 3: up3_item<T, kSector, 0>(xp, yp, H, W, s, i0, cb, clamp, wt); break;
-    case 4:
-      if constexpr (sizeof(T) == 2) up3_item<T, 8, 0>(xp, yp, H, W, s, i0, cb, clamp, wt);
+    case 0: up3_item<T, 4, 2, 2>(xp, yp, H, W, s, i0, cb, clamp, wt); break;
+    case 1: up3_item<T, 2, 2, 1>(xp, yp, H, W, s, i0, cb, clamp, wt); break;
+    case 2: up3_item<T, 4, 4, 1>(xp, yp, H, W, s, i0, cb, clamp, wt); break;
+    case 3: up3_item<T, 8, 8, 1>(xp, yp, H, W, s, i0, cb, clamp, wt); break;
+    case 4: up3_item<T, kSector, 0, 1>(xp, yp, H, W, s, i0, cb, clamp, wt); break;
+    case 5:
+      if constexpr (sizeof(T) == 2) up3_item<T, 8, 0, 1>(xp, yp, H, W, s, i0, cb, clamp, wt);
       break;
-    case 5: up3_item<T, 4, 0>(xp, yp, H, W, s, i0, cb, clamp, wt); break;
-    case 6: up3_item<T, 2, 0>(xp, yp, H, W, s, i0, cb, clamp, wt); break;
-    default: up3_item<T, 1, 0>(xp, yp, H, W, s, i0, cb, clamp, wt); break;
+    case 6: up3_item<T, 4, 0, 1>(xp, yp, H, W, s, i0, cb, clamp, wt); break;
+    case 7: up3_item<T, 2, 0, 1>(xp, yp, H, W, s, i0, cb, clamp, wt); break;
+    default: up3_item<T, 1, 0, 1>(xp, yp, H, W, s, i0, cb, clamp, wt); break;
   }
 }
 

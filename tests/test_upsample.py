@@ -87,12 +87,14 @@ def test_upsample_conv2d_fp32(giga, K, border, shape, scale):
 @pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
 @pytest.mark.parametrize("offset", [0, 1])
 @pytest.mark.parametrize("border", ["zero", "clamp"])
-def test_polyphase_store_widths(giga, scale, dtype, offset, border):
+@pytest.mark.parametrize("hw", [(70, 37), (37, 70)])
+def test_polyphase_store_widths(giga, scale, dtype, offset, border, hw):
     """The K = 3 polyphase kernel at every store width: s a multiple of 8, 4,
     2 or odd, FP32 and BF16, the output at an aligned address or one element
     past it (scalar stores), widths and heights that leave partial warps and
-    CTAs (W = 37: lanes past the image; H = 70: a second row block)."""
-    shape = (1, 2, 70, 37)
+    items (W = 37: lanes past the image; H = 70: a second row group; W = 70,
+    even: two input pixels per lane at s = 2, a partial second column block)."""
+    shape = (1, 2) + hw
     x, w = make(shape, 3, 900 + scale + offset, dtype)
     out_shape = shape[:2] + (shape[2] * scale, shape[3] * scale)
     n_out = int(np.prod(out_shape))
