@@ -895,15 +895,23 @@ def run_giga(args):
     if cached:
         L.giga_autotune_set_mode(1)
         L.check(L.giga_autotune_load(args.tune_cache), "giga_autotune_load")
-    if args.pin_bwd is not None:
+    pinned = args.pin_bwd is not None or args.pin_fwd is not None
+    if pinned:
         L.giga_autotune_set_mode(1)
     if not args.no_tune:
         for K in KS:
             d = descs[K]
-            if args.pin_bwd is not None:
-                L.check(L.giga_autotune_set_choice(d, L.GIGA_OP_BWD_INPUT | L.GIGA_OP_BWD_FILTER,
-                                                   args.pin_bwd), "giga_autotune_set_choice")
-                tuned[K] = {"fwd": L.giga_autotune_choice(d, L.GIGA_OP_FWD), "bwd": args.pin_bwd}
+            if pinned:  # pinned ops use the given candidate, the others their default
+                if args.pin_fwd is not None:
+                    L.check(L.giga_autotune_set_choice(d, L.GIGA_OP_FWD, args.pin_fwd),
+                            "giga_autotune_set_choice")
+                if args.pin_bwd is not None:
+                    L.check(L.giga_autotune_set_choice(
+                        d, L.GIGA_OP_BWD_INPUT | L.GIGA_OP_BWD_FILTER, args.pin_bwd),
+                        "giga_autotune_set_choice")
+                tuned[K] = {"fwd": L.giga_autotune_choice(d, L.GIGA_OP_FWD),
+                            "bwd": L.giga_autotune_choice(d, L.GIGA_OP_BWD_INPUT |
+                                                          L.GIGA_OP_BWD_FILTER)}
                 continue
             if cached:
                 tuned[K] = {"fwd": L.giga_autotune_choice(d, L.GIGA_OP_FWD),
@@ -1188,6 +1196,10 @@ def main():
                     help="backward configuration id for every K instead of tuning it "
                          "(0-4: fused kernel, tiles per CTA auto/2/4/8/16; 5: two passes; "
                          "6: persistent kernel with a two-stage tile ring)")
+    ap.add_argument("--pin-fwd", type=int, default=None,
+                    help="forward configuration id for every K instead of tuning it (bits: "
+                         "1 = 32-row tiles, 2 = persistent CTAs with a two-stage tile ring, "
+                         "4 = L2 prefetch of a later tile)")
     ap.add_argument("--tune-cache", default="",
                     help="autotune cache file: load it and skip tuning if it exists, "
                          "else tune and save the choices there")
