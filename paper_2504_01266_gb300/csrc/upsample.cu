@@ -1,8 +1,10 @@
 // upsample.cu -- nearest-neighbour upsampling by an integer factor s (the
 // GigaAPI paper, Section 4.2.3) and the paper's sharpening benchmark fused
 // into one pass (Section 6.6): the K x K depthwise filter applied to the
-// upsampled image, whose pixels are read straight from the small input while
-// a tile is staged, so the upsampled image never goes to HBM.
+// upsampled image without storing it.  K = 3 (the paper's Laplacian) runs the
+// polyphase kernel, which applies the taps summed per input pixel to the input
+// directly; larger K run the tile kernel, which expands the staged input rows
+// in shared memory and filters them.
 //
 //   up[n][c][p][q] = x[n][c][p / s][q / s]                      (integer division)
 //   y[n][c][p][q]  = sum_{a,b} w[c][a][b] * up~[n][c][p + a - r][q + b - r]
