@@ -1195,7 +1195,7 @@ def main():
     ap.add_argument("--pin-bwd", type=int, default=None,
                     help="backward configuration id for every K instead of tuning it "
                          "(0-4: fused kernel, tiles per CTA auto/2/4/8/16; 5: two passes; "
-                         "6: persistent kernel with a two-stage tile ring)")
+                         "6: persistent kernel with a ring of two or three tile stages)")
     ap.add_argument("--pin-fwd", type=int, default=None,
                     help="forward configuration id for every K instead of tuning it (bits: "
                          "1 = 32-row tiles, 2 = persistent CTAs with a two-stage tile ring, "

@@ -326,7 +326,7 @@ giga_status_t giga_gray_conv2d_fwd(const giga_conv2d_desc_t* desc, const void* x
  * 4, 8, 16}, id 5 = two passes (input gradient by the forward-style kernel
  * in the forward's tuned configuration, filter gradient by the filter
  * kernel), id 6 = one persistent kernel whose CTAs stream (x, dy) tile pairs
- * through a two-stage ring (the HBM-bound small filters).  The built-in default is id 0.
+ * through a ring of two or three stages (the HBM-bound small filters).  The built-in default is id 0.
  * Modes (also from the environment variable GIGA_AUTOTUNE=off|cached|full):
  *   0 off:    always the built-in default configuration;
  *   1 cached: use a cached choice when one exists (default);

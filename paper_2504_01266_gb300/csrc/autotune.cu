@@ -49,7 +49,8 @@ int tune_mode() {
 // Forward / input gradient: {8, 4} rows per thread x {one tile per CTA,
 // persistent} x {no prefetch, L2 prefetch}; filter gradient: tiles per chunk {auto, 2, 4, 8, 16}; fused
 // backward: the fused kernel with tiles per CTA {auto, 2, 4, 8, 16}, the
-// two-pass split, or the persistent kernel with a two-stage tile ring.
+// two-pass split, or the persistent kernel with a tile ring (three stages where
+// they fit, else two).
 int tune_candidates(int op) {
   switch (op) {
     case TUNE_FWD:

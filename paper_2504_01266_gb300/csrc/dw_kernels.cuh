@@ -1360,7 +1360,11 @@ struct RingShape {
   static constexpr int ROWS = kBwdTileH + 2 * G::R;
   static constexpr int T_BYTES = round_up(ROWS * G::SP * (int)sizeof(T), 128);
   static constexpr int STAGE_BYTES = 2 * T_BYTES;  // x, then dy (both with the halo)
-  static constexpr int NS = 2;
+  // three stages where they fit (two tiles in flight while one is computed)
+  static constexpr int NS = 3 * STAGE_BYTES + 2 * Geo<K>::WPAD * 4 + 4 * AT * K * 4 + 64 <=
+                                    227 * 1024
+                                ? 3
+                                : 2;
   static constexpr int SM_W = NS * STAGE_BYTES;
   static constexpr int SM_RED = SM_W + 2 * Geo<K>::WPAD * 4;
   static constexpr int SM_BAR = round_up(SM_RED + 4 * AT * K * 4, 8);
