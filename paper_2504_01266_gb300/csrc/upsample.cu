@@ -240,15 +240,16 @@ static cudaError_t up3_launch(const UpArgs& a, cudaStream_t st) {
   constexpr int kSector = 32 / (int)sizeof(T);
   switch (up3_mode(a.s, a.y, (int)sizeof(T), a.W)) {
     case 0: return up3_launch_ce<T, 4, 2, 2>(a, st);
-    case 1: return up3_launch_ce<T, 2, 2, 1>(a, st);
-    case 2: return up3_launch_ce<T, 4, 4, 1>(a, st);
-    case 3: return up3_launch_ce<T, 8, 8, 1>(a, st);
-    case 4: return up3_launch_ce<T, kSector, 0, 1>(a, st);
-    case 5:
+    case 1: return up3_launch_ce<T, 8, 4, 2>(a, st);
+    case 2: return up3_launch_ce<T, 2, 2, 1>(a, st);
+    case 3: return up3_launch_ce<T, 4, 4, 1>(a, st);
+    case 4: return up3_launch_ce<T, 8, 8, 1>(a, st);
+    case 5: return up3_launch_ce<T, kSector, 0, 1>(a, st);
+    case 6:
       if constexpr (sizeof(T) == 2) return up3_launch_ce<T, 8, 0, 1>(a, st);
       return cudaErrorInvalidValue;
-    case 6: return up3_launch_ce<T, 4, 0, 1>(a, st);
-    case 7: return up3_launch_ce<T, 2, 0, 1>(a, st);
+    case 7: return up3_launch_ce<T, 4, 0, 1>(a, st);
+    case 8: return up3_launch_ce<T, 2, 0, 1>(a, st);
     default: return up3_launch_ce<T, 1, 0, 1>(a, st);
   }
 }

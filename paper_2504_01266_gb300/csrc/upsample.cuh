@@ -441,26 +441,28 @@ __device__ __forceinline__ void up3_item(const T* __restrict__ xp, T* __restrict
 // The compilation of the polyphase body for scale s, output address y and
 // input width W: s itself where compiled for it (2, 4, 8), else run-time s,
 // with the widest stores s, y's alignment and W allow (at most 32 bytes).
-// Mode 0: s = 2 with two input pixels per lane (one 4-element store per
-// output row; W even keeps every output row aligned); 1-3: (CE, S) = (2, 2),
-// (4, 4), (8, 8); 4: one 32-byte sector, run-time s; 5: 8 elements (BF16
-// only); 6: 4; 7: 2; 8: 1.
+// Modes 0, 1: s = 2, 4 with two input pixels per lane (one store of 2 s
+// elements per output row; W even keeps every output row aligned); 2-4:
+// (CE, S) = (2, 2), (4, 4), (8, 8); 5: one 32-byte sector, run-time s; 6: 8
+// elements (BF16 only); 7: 4; 8: 2; 9: 1.
 inline int up3_mode(int s, const void* y, int elem_bytes, int64_t W) {
   const uintptr_t yp = reinterpret_cast<uintptr_t>(y);
   auto fits = [&](int ce) { return s % ce == 0 && yp % (uintptr_t)(ce * elem_bytes) == 0; };
-  if (s == 2 && W % 2 == 0 && yp % (uintptr_t)(4 * elem_bytes) == 0) return 0;
-  if (s == 2 && fits(2)) return 1;
-  if (s == 4 && fits(4)) return 2;
-  if (s == 8 && fits(8)) return 3;
-  if (fits(32 / elem_bytes)) return 4;
-  if (elem_bytes == 2 && fits(8)) return 5;
-  if (fits(4)) return 6;
-  if (fits(2)) return 7;
-  return 8;
+  auto pair_fits = [&](int ce) { return W % 2 == 0 && yp % (uintptr_t)(ce * elem_bytes) == 0; };
+  if (s == 2 && pair_fits(4)) return 0;
+  if (s == 4 && pair_fits(8) && 8 * elem_bytes <= 32) return 1;
+  if (s == 2 && fits(2)) return 2;
+  if (s == 4 && fits(4)) return 3;
+  if (s == 8 && fits(8)) return 4;
+  if (fits(32 / elem_bytes)) return 5;
+  if (elem_bytes == 2 && fits(8)) return 6;
+  if (fits(4)) return 7;
+  if (fits(2)) return 8;
+  return 9;
 }
 
 // Input columns per item of mode m.
-__host__ __device__ constexpr int up3_cols(int m) { return m == 0 ? 64 : 32; }
+__host__ __device__ constexpr int up3_cols(int m) { return m <= 1 ? 64 : 32; }
 
 // The body of mode m (a warp-uniform switch).
 template <typename T>
@@ -470,15 +472,16 @@ __device__ __forceinline__ void up3_item_mode(int m, const T* __restrict__ xp, T
   constexpr int kSector = 32 / (int)sizeof(T);
   switch (m) {
     case 0: up3_item<T, 4, 2, 2>(xp, yp, H, W, s, i0, cb, clamp, wt); break;
-    case 1: up3_item<T, 2, 2, 1>(xp, yp, H, W, s, i0, cb, clamp, wt); break;
-    case 2: up3_item<T, 4, 4, 1>(xp, yp, H, W, s, i0, cb, clamp, wt); break;
-    case 3: up3_item<T, 8, 8, 1>(xp, yp, H, W, s, i0, cb, clamp, wt); break;
-    case 4: up3_item<T, kSector, 0, 1>(xp, yp, H, W, s, i0, cb, clamp, wt); break;
-    case 5:
+    case 1: up3_item<T, 8, 4, 2>(xp, yp, H, W, s, i0, cb, clamp, wt); break;
+    case 2: up3_item<T, 2, 2, 1>(xp, yp, H, W, s, i0, cb, clamp, wt); break;
+    case 3: up3_item<T, 4, 4, 1>(xp, yp, H, W, s, i0, cb, clamp, wt); break;
+    case 4: up3_item<T, 8, 8, 1>(xp, yp, H, W, s, i0, cb, clamp, wt); break;
+    case 5: up3_item<T, kSector, 0, 1>(xp, yp, H, W, s, i0, cb, clamp, wt); break;
+    case 6:
       if constexpr (sizeof(T) == 2) up3_item<T, 8, 0, 1>(xp, yp, H, W, s, i0, cb, clamp, wt);
       break;
-    case 6: up3_item<T, 4, 0, 1>(xp, yp, H, W, s, i0, cb, clamp, wt); break;
-    case 7: up3_item<T, 2, 0, 1>(xp, yp, H, W, s, i0, cb, clamp, wt); break;
+    case 7: up3_item<T, 4, 0, 1>(xp, yp, H, W, s, i0, cb, clamp, wt); break;
+    case 8: up3_item<T, 2, 0, 1>(xp, yp, H, W, s, i0, cb, clamp, wt); break;
     default: up3_item<T, 1, 0, 1>(xp, yp, H, W, s, i0, cb, clamp, wt); break;
   }
 }
