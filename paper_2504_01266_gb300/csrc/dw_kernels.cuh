@@ -813,10 +813,10 @@ struct SepShape {
 };
 
 template <typename T, int K>
-__global__ void __launch_bounds__(kThreads) dw_sep_kernel(
-    const __grid_constant__ CUtensorMap tmx, const T* __restrict__ x,
-    const float* __restrict__ wcol, const float* __restrict__ wrow, T* __restrict__ y, FastDiv fc,
-    int H, int W, FastDiv ftx, FastDiv fty, int clamp, int vec, int use_tma, int pf, int* err) {
+__device__ __forceinline__ void dw_sep_body(
+    const CUtensorMap& tmx, const T* __restrict__ x, const float* __restrict__ wcol,
+    const float* __restrict__ wrow, T* __restrict__ y, FastDiv fc, int H, int W, FastDiv ftx,
+    FastDiv fty, int clamp, int vec, int use_tma, int pf, int* err) {
   using G = Geo<K>;
   using GS = Geo<K, sizeof(T)>;
   using S = SepShape<K, T>;
@@ -925,6 +925,26 @@ __global__ void __launch_bounds__(kThreads) dw_sep_kernel(
   }
   store_block<T, PY>(y + (int64_t)plane * H * W, H, W, ty0 + warp * PY, tx0 + 4 * lane,
                      vec != 0, acc);
+}
+
+template <typename T, int K>
+__global__ void __launch_bounds__(kThreads) dw_sep_kernel(
+    const __grid_constant__ CUtensorMap tmx, const T* __restrict__ x,
+    const float* __restrict__ wcol, const float* __restrict__ wrow, T* __restrict__ y, FastDiv fc,
+    int H, int W, FastDiv ftx, FastDiv fty, int clamp, int vec, int use_tma, int pf, int* err) {
+  dw_sep_body<T, K>(tmx, x, wcol, wrow, y, fc, H, W, ftx, fty, clamp, vec, use_tma, pf, err);
+}
+
+// The same pass compiled for five CTAs per SM (48 registers): used for FP32
+// K = 13 and 15, whose tiles (44 KB) still fit five times in shared memory and
+// whose pass waits on its tile loads (K = 15: 0.701 -> 0.689 ms on
+// 8 x 3 x 4096^2); smaller K run near the HBM rate with the default allocation.
+template <typename T, int K>
+__global__ void __launch_bounds__(kThreads, 5) dw_sep_kernel_hi_occ(
+    const __grid_constant__ CUtensorMap tmx, const T* __restrict__ x,
+    const float* __restrict__ wcol, const float* __restrict__ wrow, T* __restrict__ y, FastDiv fc,
+    int H, int W, FastDiv ftx, FastDiv fty, int clamp, int vec, int use_tma, int pf, int* err) {
+  dw_sep_body<T, K>(tmx, x, wcol, wrow, y, fc, H, W, ftx, fty, clamp, vec, use_tma, pf, err);
 }
 
 // -------------------------------------------------------------- backward

@@ -241,7 +241,15 @@ template <typename T, int K>
 static cudaError_t sep_impl(const DwArgs& a, const float* wcol, const float* wrow,
                             cudaStream_t st) {
   using S = SepShape<K, T>;
-  cudaError_t e = set_smem_once<dw_sep_kernel<T, K>>((size_t)S::SM_BYTES);
+  // FP32 K = 13, 15: the five-CTA compilation (instantiated for those only)
+  decltype(&dw_sep_kernel<T, K>) kern = dw_sep_kernel<T, K>;
+  cudaError_t e;
+  if constexpr (sizeof(T) == 4 && (K == 13 || K == 15)) {
+    kern = dw_sep_kernel_hi_occ<T, K>;
+    e = set_smem_once<dw_sep_kernel_hi_occ<T, K>>((size_t)S::SM_BYTES);
+  } else {
+    e = set_smem_once<dw_sep_kernel<T, K>>((size_t)S::SM_BYTES);
+  }
   if (e != cudaSuccess) return e;
   const int64_t tiles_x = (a.W + kTileW - 1) / kTileW;
   const int64_t tiles_y = (a.H + S::TH - 1) / S::TH;
@@ -263,14 +271,14 @@ static cudaError_t sep_impl(const DwArgs& a, const float* wcol, const float* wro
   int& per_sm = ctas_per_sm[dev & 63];
   if (per_sm == 0) {
     int v = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, dw_sep_kernel<T, K>, kThreads,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kern, kThreads,
                                                       (size_t)S::SM_BYTES) != cudaSuccess ||
         v < 1)
       v = 1;
     per_sm = v;
   }
   const int pf = K >= 13 ? per_sm * sm_count() : 0;
-  dw_sep_kernel<T, K><<<(unsigned)grid, kThreads, (size_t)S::SM_BYTES, st>>>(
+  kern<<<(unsigned)grid, kThreads, (size_t)S::SM_BYTES, st>>>(
       tm, static_cast<const T*>(a.x), wcol, wrow, static_cast<T*>(a.y),
       make_fastdiv((uint32_t)a.C), (int)a.H, (int)a.W, make_fastdiv((uint32_t)tiles_x),
       make_fastdiv((uint32_t)tiles_y), a.border, a.vec, use_tma, pf, dw_error_word());
